@@ -1,0 +1,127 @@
+"""Imaginary-time evolution with full update and environment recycling (oracle), Sec. VI.B-C.
+
+Plain step (every row a1-a10):
+    A_c   = weighted canonical form of A, with weights lambda           (a11)
+    Theta = g A_c                                                        (a1)
+    pre   = simple-update projectors with the lambda environment         (a7)
+    a     = double layers of the pre-truncated tensors                   (a2)
+    env   = CTMRG of a, warm-started from the previous environment       (a3-a6)
+    fu    = bond environment + ALS + balance on every link               (a8-a9)
+    A~    = Theta with the fu pairs on every leg                         (a10)
+Reading: the canonical form is taken before every full update so that the
+simple-update pre-truncation has its weights; the full update itself does not
+depend on the gauge.
+
+Recycled window (Sec. VI.C steps (i)-(iii)):
+    A_0 = A_c of the current A; one plain step gives Theta, fu and A~;
+    (i)   canonical form of A~: A~_1 = A~ x_legs maps                  (a11)
+    (ii)  gauge fix: A~_1 ~ A_0 x W                                    (a12)
+    (iii) renormalised gate: per leg K = P_fu maps W^T (out legs) and
+          K = Q_fu^T maps W^T (in legs), kappa*D x D;
+          A_k = (g A_{k-1}) x_legs K, k = 1..N_Re, each max-abs normalised (a13)
+    A_0 <- A_{N_Re}.
+Reading of the printed G of Sec. VI.C: the stray "Q_v" between P_hc and P_v is
+dropped, G = U_h^+ U_v^+ Q_hc Q_h Q_vc Q_v g P_h P_hc P_v P_vc U_h U_v.
+With N_Re = 1 the window reproduces the plain step up to a gauge.
+"""
+import numpy as np
+
+from .model import ipepo, apply_pepo
+from .ctmrg import double_layer, ctmrg, init_env
+from .fullupdate import (pretruncation, pretruncated_sites, full_update, assemble,
+                         leg_links, leg_mul, LEG)
+from .canonical import canonicalize, gauge_fix
+from .observables import measure
+
+
+class Config:
+    def __init__(self, h, tau, D, chi, ctm_tol=1e-10, ctm_max=500, als_tol=1e-12, als_max=50,
+                 canon_tol=1e-12, canon_max=1000, gauge_tol=1e-12, gauge_max=500):
+        self.h, self.tau, self.D, self.chi = h, tau, D, chi
+        self.ctm_tol, self.ctm_max = ctm_tol, ctm_max
+        self.als_tol, self.als_max = als_tol, als_max
+        self.canon_tol, self.canon_max = canon_tol, canon_max
+        self.gauge_tol, self.gauge_max = gauge_tol, gauge_max
+
+
+def fu_step(A, cell, cfg, env=None, g=None):
+    """One plain imaginary-time step.  Returns (A~, env, info) with info holding the pieces."""
+    g = ipepo(cfg.h, cfg.tau) if g is None else g
+    can = canonicalize(A, cell, cfg.canon_tol, cfg.canon_max)
+    Ac = can['A']
+    Theta = [apply_pepo(g, a) for a in Ac]
+    pre = pretruncation(Theta, cell, can['lam'], cfg.D)
+    a_list = [double_layer(x) for x in pretruncated_sites(Theta, cell, pre)]
+    st, it, delta, conv = ctmrg(cell, a_list, cfg.chi, cfg.ctm_tol, cfg.ctm_max, env=env)
+    fu, als_info = full_update(Theta, cell, st, pre, cfg.als_tol, cfg.als_max)
+    At = assemble(Theta, cell, fu)
+    info = dict(A0=Ac, lam=can['lam'], Theta=Theta, pre=pre, fu=fu, ctm_iters=it,
+                ctm_delta=delta, ctm_converged=conv, als=als_info, state=st)
+    return At, st.env, info
+
+
+def gate_legs(cell, fu, maps, W):
+    """Renormalised-gate leg matrices K[(t, leg)] (kappa*D x D), step (iii)."""
+    K = {}
+    n = len({t for (t, _l) in maps})
+    for t in range(n):
+        for name, (e, side) in leg_links(cell, t).items():
+            P, Q = fu[e]
+            base = P if side == 'out' else Q.T
+            K[(t, name)] = base @ maps[(t, name)] @ W[e].T
+    return K
+
+
+def recycled_step(A, cell, g, K):
+    """A <- (g A) x_legs K, max-abs normalised (row a13)."""
+    out = []
+    for t, a in enumerate(A):
+        T = apply_pepo(g, a)
+        for name in ('l', 'r', 'd', 'u'):
+            T = leg_mul(T, LEG[name], K[(t, name)])
+        out.append(T / np.abs(T).max())
+    return out
+
+
+def recycle_window(A, cell, cfg, n_re, env=None, g=None):
+    """One environment computation followed by n_re applications of the renormalised gate."""
+    g = ipepo(cfg.h, cfg.tau) if g is None else g
+    At, env, info = fu_step(A, cell, cfg, env, g)
+    can1 = canonicalize(At, cell, cfg.canon_tol, cfg.canon_max)
+    W, F, git = gauge_fix(info['A0'], can1['A'], cell, cfg.gauge_tol, cfg.gauge_max)
+    K = gate_legs(cell, info['fu'], can1['maps'], W)
+    Ak = info['A0']
+    for _ in range(n_re):
+        Ak = recycled_step(Ak, cell, g, K)
+    info.update(F=F, gauge_iters=git, K=K, A1=can1['A'])
+    return Ak, env, info
+
+
+def evolve(A, cell, cfg, n_steps, n_re=1, recycle=False, env=None, log=None):
+    """n_steps imaginary-time steps, plain (n_re ignored) or recycled in windows of n_re steps.
+
+    Returns (A, env, number of environment computations).
+    """
+    done, n_env = 0, 0
+    while done < n_steps:
+        if recycle:
+            k = min(n_re, n_steps - done)
+            A, env, info = recycle_window(A, cell, cfg, k, env)
+            done += k
+        else:
+            A, env, info = fu_step(A, cell, cfg, env)
+            done += 1
+        n_env += 1
+        if log is not None:
+            log.append(dict(step=done, ctm_iters=info['ctm_iters'], F=info.get('F')))
+    return A, env, n_env
+
+
+def energy(A, cell, cfg, env=None, tol=1e-10, max_iter=500):
+    """CTMRG on the double layers of A, then the observables of Sec. VI.D."""
+    a_list = [double_layer(x) for x in A]
+    st, it, delta, conv = ctmrg(cell, a_list, cfg.chi, tol, max_iter, env=env)
+    m = measure(st, cell, A, cfg.h)
+    m.update(ctm_iters=it, ctm_delta=delta, ctm_converged=conv, env=st.env)
+    return m
+

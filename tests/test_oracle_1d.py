@@ -1,0 +1,75 @@
+"""Pins of the 1D oracle: canonical form, gauge fixing, iTEBD and recycling (Sec. III, V)."""
+import numpy as np
+import pytest
+from scipy.stats import ortho_group
+
+from oracle import imps, model
+from paper_1411_0391_gb300.inputs import random_matrix
+
+
+def _random_mps(chi, instance):
+    A = random_matrix((2, chi, chi), instance=instance)
+    return A / np.abs(A).max()
+
+
+def test_canonical_constraints():
+    """Sum_s Gamma^T lambda^2 Gamma = I and Sum_s Gamma lambda^2 Gamma^T = I up to a scalar (Sec. III.A)."""
+    G, lam, ML, MR, Aw = imps.canonicalize(_random_mps(6, 1), tol=1e-14)
+    VL = np.einsum('slr,l,slq->rq', G, lam ** 2, G)
+    VR = np.einsum('slr,r,sqr->lq', G, lam ** 2, G)
+    for V in (VL, VR):
+        np.testing.assert_allclose(V / V[0, 0], np.eye(6), atol=1e-10)
+    assert np.all(np.diff(lam) <= 1e-15)
+
+
+def test_canonical_form_is_gauge_invariant():
+    """Two iMPS related by an invertible gauge (Sec. II.A) share the canonical weights."""
+    A = _random_mps(5, 2)
+    X = np.eye(5) + 0.3 * random_matrix((5, 5), instance=3)
+    B = np.einsum('ab,sbc,cd->sad', X, A, np.linalg.inv(X))
+    la = imps.canonicalize(A, tol=1e-14)[1]
+    lb = imps.canonicalize(B, tol=1e-14)[1]
+    np.testing.assert_allclose(la, lb, atol=1e-10)
+
+
+def test_gauge_fix_recovers_orthogonal_gauge():
+    """B = U A U^T with U orthogonal: the iterative method of Sec. III.B.2 reaches F = 1."""
+    Aw = imps.canonicalize(_random_mps(5, 4), tol=1e-14)[4]
+    U = ortho_group.rvs(5, random_state=7)
+    B = np.einsum('ab,sbc,dc->sad', U, Aw, U)
+    Ufound, F = imps.gauge_fix(Aw, B)
+    assert abs(F - 1.0) < 1e-10
+    np.testing.assert_allclose(np.einsum('ab,sbc,dc->sad', Ufound, Aw, Ufound), B, atol=1e-8)
+
+
+@pytest.mark.slow
+def test_itebd_reaches_closed_form():
+    """iTEBD with the iMPO converges to e(h) of the infinite chain (Sec. V.A); h = 3, chi = 6."""
+    h = 3.0
+    A = imps.itebd(_random_mps(6, 5), h, 0.05, 6, 40)
+    A = imps.itebd(A, h, 0.01, 6, 60)
+    e = imps.observables(A, h)[2]
+    assert abs(e - model.exact_energy_1d(h)) < 1e-6
+
+
+def test_recycling_nre1_equals_plain_step():
+    """One recycling window with N_Re = 1 is the plain step up to a gauge (Sec. V.B)."""
+    h, d, chi = 2.0, 0.05, 5
+    A = imps.itebd(_random_mps(chi, 6), h, d, chi, 10)
+    plain = imps.itebd(A, h, d, chi, 1)
+    rec, F = imps.recycle_window(A, h, d, chi, 1)
+    assert F <= 1.0 + 1e-12
+    for a, b in zip(imps.observables(plain, h), imps.observables(rec, h)):
+        assert abs(a - b) < 1e-9
+
+
+@pytest.mark.slow
+def test_recycling_reaches_same_ground_state():
+    """Recycled windows (N_Re = 4) reach the same energy as plain iTEBD (Sec. V.C)."""
+    h, chi = 3.0, 6
+    A0 = imps.itebd(_random_mps(chi, 8), h, 0.05, chi, 30)
+    A = A0
+    for _ in range(15):
+        A, F = imps.recycle_window(A, h, 0.01, chi, 4)
+    e_rec = imps.observables(A, h)[2]
+    assert abs(e_rec - model.exact_energy_1d(h)) < 1e-5

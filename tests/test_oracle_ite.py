@@ -1,0 +1,73 @@
+"""End-to-end pins of the 2D imaginary-time evolution with full update and recycling (Sec. VI).
+
+D = 1 restricts the iPEPS to product states; imaginary-time evolution then
+converges (error O(tau^2)) to the mean-field optimum E_site = -2 - h^2/8
+(h < 4), which fixes the iPEPO, the double layer, the bond environment, the
+ALS solve and the assembly together.  At h = 0 the ferromagnetic product state
+is an exact fixed point with E_site = -2.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ctmrg as C
+from oracle import recycle as R
+from paper_1411_0391_gb300.inputs import random_peps
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("h", [2.0, 3.0])
+def test_d1_reaches_mean_field(h):
+    cell = C.checkerboard()
+    A = random_peps(2, 1, instance=3)
+    cfg = R.Config(h=h, tau=0.05, D=1, chi=2)
+    A, env, _ = R.evolve(A, cell, cfg, 100)
+    cfg.tau = 0.01
+    A, env, _ = R.evolve(A, cell, cfg, 200, env=env)
+    m = R.energy(A, cell, cfg)
+    assert abs(m['e_site'] - (-2.0 - h * h / 8.0)) < 1e-4
+    assert abs(np.mean(list(m['mx'].values())) - h / 4.0) < 1e-2     # first order in the state error
+
+
+def test_d1_recycled_reaches_mean_field():
+    h = 2.0
+    cell = C.checkerboard()
+    A = random_peps(2, 1, instance=4)
+    cfg = R.Config(h=h, tau=0.05, D=1, chi=2)
+    A, env, _ = R.evolve(A, cell, cfg, 60)
+    cfg.tau = 0.01
+    A, env, n_env = R.evolve(A, cell, cfg, 200, n_re=5, recycle=True, env=env)
+    assert n_env == 40
+    m = R.energy(A, cell, cfg)
+    assert abs(m['e_site'] - (-2.0 - h * h / 8.0)) < 1e-4
+
+
+def test_h0_product_state_is_fixed_point():
+    cell = C.checkerboard()
+    A = np.zeros((2, 2, 2, 2, 2))
+    A[0, 0, 0, 0, 0] = 1.0
+    A = A + 1e-6 * np.random.default_rng(0).standard_normal(A.shape)
+    A = [A, A.copy()]
+    cfg = R.Config(h=0.0, tau=0.01, D=2, chi=4)
+    env = None
+    for _ in range(5):
+        A, env, _ = R.fu_step(A, cell, cfg, env)
+    m = R.energy(A, cell, cfg)
+    assert abs(m['e_site'] + 2.0) < 1e-10
+
+
+@pytest.mark.slow
+def test_large_field_against_exact_diagonalisation():
+    """h = 5: D = 2 full update against the 4x4 torus ground state (loose: D = 2 and finite size)."""
+    with open(os.path.join(GOLDEN, "ed_4x4.json")) as f:
+        e_ed = json.load(f)["tfim_4x4_e_site_h5.0"]
+    cell = C.checkerboard()
+    A = random_peps(2, 2, instance=5)
+    cfg = R.Config(h=5.0, tau=0.02, D=2, chi=12, ctm_max=200)
+    A, env, _ = R.evolve(A, cell, cfg, 80)
+    m = R.energy(A, cell, cfg)
+    assert abs(m['e_site'] - e_ed) < 3e-3
+    assert m['e_site'] > e_ed - 1e-4          # a variational state cannot go below the ground state by more than finite-size effects
