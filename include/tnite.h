@@ -1,0 +1,240 @@
+/*
+ * tnite.h - C ABI of the GB300 (sm_103a) library for imaginary-time evolution
+ * of an infinite PEPS with CTMRG environments, full-update truncation and
+ * environment recycling.
+ *
+ * Method: Phien, McCulloch, Vidal, "Faster convergence of imaginary time
+ * evolution tensor network algorithms by recycling the environment"
+ * (arXiv:1411.0391).  Section/equation numbers below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All floating point data is IEEE double, row-major (C order).
+ *  - Site tensor A[s][l][r][d][u], physical dimension d = 2, bond dimension D;
+ *    x grows to the right, y downward; A's r leg joins the l leg of the site
+ *    to its right, its d leg the u leg of the site below.
+ *  - Unit cells: TN_CELL_CHECKERBOARD holds tensors A (id 0) and B (id 1) in
+ *    the pattern [[A, B], [B, A]]; TN_CELL_SINGLE holds one tensor.
+ *  - A "state" buffer is the concatenation of the cell's tensors in id order,
+ *    n_tensors * d * D^4 doubles.
+ *  - Status codes: every int-returning call returns TN_OK (0) or a negative
+ *    TN_E* code; tn_strerror() gives a message.  TN_ENOCONV is a warning: the
+ *    results are written and usable, an iteration cap was hit.
+ *  - Ownership: the caller owns every host and device buffer it passes.  A
+ *    context never allocates device memory: all of it is carved from the
+ *    device workspace given to tn_create (size from tn_workspace_bytes).
+ *    Host buffers may be freed as soon as a call returns (the library copies).
+ *  - Streams: a context enqueues all its work on the CUDA stream given to
+ *    tn_create and synchronises that stream before returning from any call
+ *    that reports host-visible results.  A context is not thread-safe.
+ */
+#ifndef TNITE_H
+#define TNITE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define TN_OK         0
+#define TN_EINVAL    -1   /* bad argument: null pointer, size, D > chi, tau <= 0 ... */
+#define TN_ENOMEM    -2   /* workspace too small */
+#define TN_ECUDA     -3   /* a CUDA runtime call failed */
+#define TN_ENOCONV   -4   /* iteration cap reached (warning; results written) */
+#define TN_ENUMERIC  -5   /* NaN or Inf detected */
+#define TN_ESTATE    -6   /* call out of order (e.g. no state set) */
+
+/* ---- configuration ------------------------------------------------------ */
+#define TN_CELL_CHECKERBOARD 2
+#define TN_CELL_SINGLE       1
+
+#define TN_F64    0   /* every contraction in double */
+
+typedef struct tn_config {
+    int D;          /* PEPS bond dimension, 1..8 */
+    int chi;        /* CTM bond dimension, 1 <= chi <= 96 */
+    int cell;       /* TN_CELL_CHECKERBOARD or TN_CELL_SINGLE */
+    int precision;  /* TN_F64 */
+} tn_config;
+
+/* Number of kernels this library has launched in the process so far (all
+ * contexts); a monotone counter for accounting, no synchronisation implied. */
+unsigned long long tn_launch_count(void);
+
+/* Bytes of device workspace a context with this configuration needs
+ * (256-byte aligned base).  Returns 0 for an invalid configuration. */
+size_t tn_workspace_bytes(const tn_config* cfg);
+
+/* Create a context.  d_workspace: device pointer of at least
+ * tn_workspace_bytes(cfg) bytes, owned by the caller and kept alive until
+ * tn_destroy.  stream: a cudaStream_t (NULL = legacy default stream). */
+int  tn_create(void** out_ctx, const tn_config* cfg, void* d_workspace,
+               size_t workspace_bytes, void* stream);
+void tn_destroy(void* ctx);
+const char* tn_strerror(int status);
+
+/* ---- problem definition (Sec. V.A, VI.A) -------------------------------- */
+/* Transverse-field Ising model H = -J sum_<ij> Z_i Z_j - h sum_i X_i.
+ * Reading: J = 1 is the paper's model; other J > 0 rescale the ZZ term. */
+int tn_set_hamiltonian(void* ctx, double J, double h);
+/* Trotter step tau > 0: rebuilds the iPEPO g of Sec. VI.A, Fig. 20 (row a1):
+ * g = g_F (bond halves on l, r, d, u) g_F, kappa = 2. */
+int tn_set_time_step(void* ctx, double tau);
+
+/* Copy the iPEPS tensors in (n = n_tensors*d*D^4 doubles, host memory). */
+int tn_set_state(void* ctx, const double* host, size_t n);
+int tn_get_state(void* ctx, double* host, size_t n);
+
+/* ---- environment: CTMRG (Sec. VI.B item 1, Fig. 21a; rows a2-a6) -------- */
+typedef struct tn_ctm_report {
+    int    iterations;   /* CTMRG iterations done (one = left, up, right, down move) */
+    int    converged;    /* 1 if delta < tol */
+    double delta;        /* max over corners of ||s_new - s_old||_2 of the
+                            sum-normalised corner singular values */
+} tn_ctm_report;
+
+/* Build the double layers a = sum_s A^s (x) A^s of the current state (row a2),
+ * with the ket and bra legs fused ket*D + bra. */
+int tn_build_double_layer(void* ctx);
+/* Replace the double layers by an arbitrary network: a_host holds one tensor
+ * a[l][r][d][u] per tensor id, each leg of dimension leg_dim (leg_dim <= D^2
+ * of the configuration); boundary (leg_dim doubles) is the vector of the
+ * trivial initial boundary (NULL: the ket-bra identity, leg_dim = D^2). */
+int tn_set_network(void* ctx, const double* a_host, int leg_dim, const double* boundary);
+/* Reset the environment to the trivial boundary (bond 1 padded to chi). */
+int tn_reset_env(void* ctx);
+/* Run CTMRG iterations on the current double layers, warm-started from the
+ * context's environment, until the corner-spectrum change is below tol or
+ * max_iter iterations.  Returns TN_OK or TN_ENOCONV. */
+int tn_ctmrg(void* ctx, double tol, int max_iter, tn_ctm_report* rep);
+/* Run n_moves directional moves (left, up, right, down, left, ...) without a
+ * convergence test; a move absorbs every column of the cell (rows a3-a5). */
+int tn_ctmrg_moves(void* ctx, int n_moves);
+/* Environment in/out: per site (x, y) in row-major cell order, C1..C4
+ * (chi x chi each) then T1..T4 (chi x chi x leg_dim each), C[in][out] and
+ * T[in][out][m] with the clockwise in/out convention of Fig. 21a. */
+size_t tn_env_size(void* ctx);
+int tn_get_env(void* ctx, double* host, size_t n);
+int tn_set_env(void* ctx, const double* host, size_t n);
+/* Corner spectra (row a6): s / sum(s) of every corner, sorted descending:
+ * out[(site*4 + corner)*chi + i]; n = n_sites*4*chi. */
+int tn_corner_spectra(void* ctx, double* host, size_t n);
+/* Contractions of one site's environment with a tensor a (leg_dim legs):
+ * out[0] = Z1 (with a), out[1] = Z0 (corners only), out[2] = Zh (T1, T3),
+ * out[3] = Zv (T2, T4); a_host NULL uses the site's own double layer. */
+int tn_site_scalars(void* ctx, int site, const double* a_host, double out[4]);
+
+/* ---- one imaginary-time step (Sec. VI.B, VI.C; rows a1, a7-a13) --------- */
+typedef struct tn_step_report {
+    int    canon_iters;     /* canonical-form iterations of the state (a11) */
+    int    ctm_iterations;  /* CTMRG iterations of this step (a3-a6) */
+    double ctm_delta;
+    int    als_iters[8];    /* ALS sweeps per link type (a9) */
+    double als_cost[8];     /* final cost f / <g|g> per link type */
+} tn_step_report;
+
+/* Prepare a full-update step: canonical form of the state (a11, with its
+ * weights lambda), Theta = g A_c (a1), simple-update pre-truncation (a7) and
+ * the double layers of the pre-truncated tensors (a2). */
+int tn_step_prepare(void* ctx, tn_step_report* rep);
+/* Bond environment (a8), ALS (a9) and assembly (a10) on every link type; the
+ * state becomes A~ = Q Theta P (max-abs normalised).  Requires a prior
+ * tn_step_prepare and tn_ctmrg. */
+int tn_step_update(void* ctx, tn_step_report* rep);
+/* Plain full-update step: prepare, CTMRG(ctm_tol, ctm_max), update. */
+int tn_fu_step(void* ctx, double ctm_tol, int ctm_max, tn_step_report* rep);
+
+/* Recycling window of Sec. VI.C: after tn_step_prepare + tn_ctmrg +
+ * tn_step_update, build the renormalised gate (canonical form of A~ (a11),
+ * gauge fix against A_0 (a12), leg matrices K (a13)); the state is reset to
+ * A_0 and then advanced by n_re applications A <- (g A) x_legs K.
+ * fidelity (optional out): the local fidelity F of Eq. (25). */
+int tn_recycle(void* ctx, int n_re, double* fidelity);
+
+typedef struct tn_evolve_opts {
+    int    recycle;        /* 0: plain full update every step; 1: recycle */
+    int    n_re;           /* steps per environment computation (recycle = 1) */
+    double ctm_tol;        /* CTMRG tolerance per environment computation */
+    int    ctm_max;        /* CTMRG iteration cap */
+} tn_evolve_opts;
+
+typedef struct tn_evolve_report {
+    int    steps;          /* imaginary-time steps done */
+    int    env_computations;
+    int    ctm_iterations; /* total CTMRG iterations */
+    int    ctm_moves;      /* total directional moves */
+    int    nonconverged;   /* environment computations that hit ctm_max */
+    double last_fidelity;  /* F of the last recycling window (recycle = 1) */
+} tn_evolve_report;
+
+/* n_steps imaginary-time steps (Sec. VI.B-C). */
+int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* opts, tn_evolve_report* rep);
+
+/* ---- observables (Sec. VI.D; row a14) ----------------------------------- */
+typedef struct tn_observables {
+    double e_site;    /* -(1/n) sum_links <ZZ> J - h (1/n) sum_t <X>_t */
+    double e_link;    /* e_site / 2 */
+    double mx[2];     /* <X> per tensor id */
+    double mz[2];     /* <Z> per tensor id */
+    double zz[4];     /* <Z Z> per link type: (A,h), (B,h), (A,v), (B,v) */
+} tn_observables;
+
+/* Observables of the current state from the current environment (which must
+ * be the environment of the state's own double layers: call
+ * tn_build_double_layer + tn_ctmrg first). */
+int tn_measure(void* ctx, tn_observables* obs);
+
+/* ---- intermediate tensors (for checkpoints and parity checks) ----------- */
+#define TN_T_STATE      0   /* A per tensor id: d*D^4 */
+#define TN_T_CANON      1   /* weighted canonical tensors A_c (a11): d*D^4 */
+#define TN_T_LAMBDA     2   /* canonical weights per link type: D */
+#define TN_T_THETA      3   /* Theta = g A_c per tensor id: d*(2D)^4 */
+#define TN_T_PRE_P      4   /* pre-truncation P per link type: 2D x D */
+#define TN_T_PRE_Q      5   /* pre-truncation Q per link type: D x 2D */
+#define TN_T_DOUBLE     6   /* double layer per tensor id: D^8 (a[l][r][d][u]) */
+#define TN_T_BOND_ENV   7   /* normalised, PSD bond environment per link type:
+                               N4[a][b][a'][b'], (2D)^4 */
+#define TN_T_FU_P       8   /* full-update P per link type (balanced) */
+#define TN_T_FU_Q       9   /* full-update Q per link type */
+#define TN_T_GAUGE_W   10   /* gauge matrices W per link type: D x D */
+#define TN_T_GATE_K    11   /* renormalised-gate leg matrices per (tensor, leg l,r,d,u): 2D x D */
+#define TN_T_PEPO      12   /* iPEPO g[s'][s][l][r][d][u]: d*d*16 */
+
+/* Copy one intermediate tensor to host; index = tensor id, link type (in the
+ * order (A,h), (B,h), (A,v), (B,v); (A,h), (A,v) for the 1-site cell) or
+ * tensor*4 + leg.  n must equal the tensor's size (see list above). */
+int tn_get_tensor(void* ctx, int which, int index, double* host, size_t n);
+
+/* ---- kernel-level entry points (device pointers, used by the parity tests
+ *      and usable on their own) ----------------------------------------- */
+/* Batched strided C = alpha op(A) op(B) + beta C in double; op = transpose
+ * when trans* = 1.  A is m x k (or k x m if transA), row-major with leading
+ * dimension lda; likewise B, C; strides in elements between batch entries. */
+int tn_gemm_f64(int transA, int transB, int m, int n, int k, double alpha,
+                const double* dA, int lda, long long strideA,
+                const double* dB, int ldb, long long strideB, double beta,
+                double* dC, int ldc, long long strideC, int batch, void* stream);
+/* Permute a rank <= 8 tensor: out[i_perm[0]]...[i_perm[r-1]] = in[i_0]..[i_{r-1}],
+ * i.e. output axis j is input axis perm[j]; dims are the input dims. */
+int tn_permute_f64(const double* d_in, double* d_out, int rank, const int* dims,
+                   const int* perm, void* stream);
+/* One-sided Jacobi SVD of batch matrices m x n (n <= m <= 112, row-major,
+ * consecutive): S descending (batch x n), U (batch x m x n), V (batch x n x n),
+ * sign rule: the entry of largest |.| of each column of U is positive. */
+int tn_svd_small(const double* dA, int m, int n, int batch, double* dU, double* dS,
+                 double* dV, void* stream);
+/* Symmetric Jacobi eigendecomposition of batch n x n matrices (n <= 112):
+ * eigenvalues ascending (batch x n), eigenvectors as columns of dV. */
+int tn_eigh_small(const double* dA, int n, int batch, double* dW, double* dV, void* stream);
+/* Top-k singular triplets of one m x m matrix (device), k <= 96: U (m x k),
+ * S (k), V (m x k), sign rule applied; warm (optional, m x k) is a starting
+ * right basis.  Subspace iteration with Rayleigh-Ritz for m > 112. */
+int tn_truncated_svd(void* ctx, const double* dM, int m, int k, double* dU, double* dS,
+                     double* dV, const double* warm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNITE_H */

@@ -171,17 +171,24 @@ def fidelity(A, B, cell, W):
     return float(sum(np.sum(a * b) for a, b in zip(At, B)) / len(A))
 
 
-def gauge_fix(A, B, cell, tol=1e-12, max_iter=500):
+def polar(M):
+    """Orthogonal polar factor U V^T of M = U S V^T."""
+    U, S, Vt = np.linalg.svd(M)
+    return U @ Vt
+
+
+def gauge_fix(A, B, cell, tol=1e-12, max_iter=500, W0=None):
     """Orthogonal link matrices W with B ~ A x W maximising the local fidelity (row a12).
 
     A and B are weighted canonical tensors with ||A_t|| = ||B_t|| = 1.  The
-    links are visited in link_list order; the iteration stops when no W_e
-    changes by more than tol in one pass (F is quadratic in the error of W near
-    its maximum, so F itself is a poor stopping rule).  Returns W, F, passes.
+    iteration starts from W0 (default: identities; the paper allows any start)
+    and visits the links in link_list order; it stops when no W_e changes by
+    more than tol in one pass (F is quadratic in the error of W near its
+    maximum, so F itself is a poor stopping rule).  Returns W, F, passes.
     """
     D = A[0].shape[1]
     links = link_list(cell)
-    W = {e: np.eye(D) for e in links}
+    W = {e: np.eye(D) for e in links} if W0 is None else {e: W0[e].copy() for e in links}
     it = 0
     for it in range(1, max_iter + 1):
         change = 0.0

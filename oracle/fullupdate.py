@@ -149,24 +149,66 @@ def truncate_legs(T, cell, t, proj, open_leg=None):
     return T
 
 
+def _un(T):
+    c = T.shape[0]
+    D = int(round(np.sqrt(T.shape[2])))
+    return T.reshape(c, c, D, D)
+
+
+def _ein(spec, x, y):
+    return np.einsum(spec, x, y, optimize=True)
+
+
+def half_env_left(e, Tp, bra=None, open_phys=False):
+    """E_L[o, n, R, r(, s, s')] of site p: C1 T1 T4 with the ket and bra of Tp, then C4 T3.
+
+    Contracted pairwise (the order keeps every intermediate at chi^2 D^4 size):
+    C1 T1 -> T4 -> ket -> bra -> (C4 T3).  Tp's r leg stays open (ket R, bra r);
+    with open_phys the physical legs stay open too.
+    """
+    bra = Tp if bra is None else bra
+    chi, D = e['C1'].shape[0], Tp.shape[1]
+    X1 = _ein('ia,aom->iom', e['C1'], e['T1'])
+    X2 = _ein('iom,jin->omjn', X1, e['T4']).reshape(chi, D, D, chi, D, D)
+    X3 = _ein('oUujLl,sLRDU->oujlsRD', X2, Tp)
+    if open_phys:
+        X4 = _ein('oujlsRD,tlrdu->ojRDrdst', X3, bra)
+    else:
+        X4 = _ein('oujlsRD,slrdu->ojRDrd', X3, bra)
+    LL = _ein('kj,nkm->jnm', e['C4'], e['T3']).reshape(chi, chi, D, D)
+    if open_phys:
+        return _ein('ojRDrdst,jnDd->onRrst', X4, LL)
+    return _ein('ojRDrd,jnDd->onRr', X4, LL)
+
+
+def half_env_right(e, Tq, bra=None, open_phys=False):
+    """E_R[o, n, L, l(, s, s')] of site q: T1 C2 T2 with the ket and bra of Tq, then C3 T3."""
+    bra = Tq if bra is None else bra
+    chi, D = e['C2'].shape[0], Tq.shape[2]
+    Y1 = _ein('oam,ac->ocm', e['T1'], e['C2'])
+    Y2 = _ein('ocm,ctn->omtn', Y1, e['T2']).reshape(chi, D, D, chi, D, D)
+    Y3 = _ein('oUutRr,sLRDU->outrsLD', Y2, Tq)
+    if open_phys:
+        Y4 = _ein('outrsLD,plrdu->otLDldsp', Y3, bra)
+    else:
+        Y4 = _ein('outrsLD,slrdu->otLDld', Y3, bra)
+    LR = _ein('te,enm->tnm', e['C3'], e['T3']).reshape(chi, chi, D, D)
+    if open_phys:
+        return _ein('otLDldsp,tnDd->onLlsp', Y4, LR)
+    return _ein('otLDld,tnDd->onLl', Y4, LR)
+
+
 def bond_env_h(ep, eq, Tp, Tq):
     """N[a, a', b, b'] of the horizontal link p -> q (Fig. 21b; reading of E1..E6).
 
     ep, eq: environments of p and q; Tp has its r leg open, Tq its l leg open
     (ket a, bra a' for p; ket b, bra b' for q).  E_L collects C1 T1 T4 C4 T3 of
-    p with the two layers of Tp, E_R collects C2 T1 T2 C3 T3 of q with Tq.
+    p with the two layers of Tp, E_R collects C2 T1 T2 C3 T3 of q with Tq;
+    T1_p.out joins T1_q.in and T3_q.out joins T3_p.in.
     """
-    def un(T):
-        c = T.shape[0]
-        D = int(round(np.sqrt(T.shape[2])))
-        return T.reshape(c, c, D, D)
-    EL = np.einsum('ia,aoUu,jiLl,kj,nkDd,sLRDU,slrdu->onRr',
-                   ep['C1'], un(ep['T1']), un(ep['T4']), ep['C4'], un(ep['T3']), Tp, Tp,
-                   optimize='greedy')
-    ER = np.einsum('ab,oaUu,bcRr,ce,enDd,sLRDU,slrdu->onLl',
-                   eq['C2'], un(eq['T1']), un(eq['T2']), eq['C3'], un(eq['T3']), Tq, Tq,
-                   optimize='greedy')
-    return np.einsum('onAa,onBb->AaBb', EL, ER)
+    EL = half_env_left(ep, Tp)
+    ER = half_env_right(eq, Tq)
+    return np.einsum('onAa,onBb->AaBb', EL, ER, optimize=True)
 
 
 def bond_env(st, cell, e, Theta, proj):

@@ -14,31 +14,33 @@ import numpy as np
 
 from .model import X, Z
 from .ctmrg import rotate_site
-from .fullupdate import neighbours, link_list
+from .fullupdate import neighbours, link_list, half_env_left, half_env_right
 
 
-def _un(T):
-    c = T.shape[0]
-    D = int(round(np.sqrt(T.shape[2])))
-    return T.reshape(c, c, D, D)
+def _ein(spec, x, y):
+    return np.einsum(spec, x, y, optimize=True)
 
 
 def rdm1(e, A):
-    """rho[s, s'] of one site from its eight environment tensors (trace not normalised)."""
-    return np.einsum('ia,aoUu,ob,bcRr,ce,enDd,nk,kiLl,sLRDU,tlrdu->st',
-                     e['C1'], _un(e['T1']), e['C2'], _un(e['T2']), e['C3'], _un(e['T3']),
-                     e['C4'], _un(e['T4']), A, A, optimize='greedy')
+    """rho[s, s'] of one site from its eight environment tensors (trace not normalised).
+
+    Pairwise: top = C1 T1 C2, bottom = C3 T3 C4, then T2, T4, the ket and the bra.
+    """
+    chi, D = e['C1'].shape[0], A.shape[1]
+    top = _ein('ibm,bc->icm', _ein('ia,abm->ibm', e['C1'], e['T1']), e['C2'])
+    bot = _ein('dfx,fj->djx', _ein('de,efx->dfx', e['C3'], e['T3']), e['C4'])
+    R1 = _ein('icm,cdn->imdn', top, e['T2'])
+    R2 = _ein('imdn,djx->imnjx', R1, bot)
+    R3 = _ein('imnjx,jil->mnxl', R2, e['T4']).reshape((D,) * 8)     # [(U u), (R r), (D d), (L l)]
+    K1 = _ein('UuRrDdLl,sLRDU->urdls', R3, A)
+    return _ein('urdls,tlrdu->st', K1, A)
 
 
 def rdm2_h(ep, eq, Ap, Aq):
     """rho[s, t, s', t'] of the horizontal pair p -> q (trace not normalised)."""
-    EL = np.einsum('ia,aoUu,jiLl,kj,nkDd,sLRDU,plrdu->onRrsp',
-                   ep['C1'], _un(ep['T1']), _un(ep['T4']), ep['C4'], _un(ep['T3']), Ap, Ap,
-                   optimize='greedy')
-    ER = np.einsum('ab,oaUu,bcRr,ce,enDd,sLRDU,plrdu->onLlsp',
-                   eq['C2'], _un(eq['T1']), _un(eq['T2']), eq['C3'], _un(eq['T3']), Aq, Aq,
-                   optimize='greedy')
-    return np.einsum('onABsp,onABtq->stpq', EL, ER)
+    EL = half_env_left(ep, Ap, open_phys=True)       # [o, n, R, r, s, s']
+    ER = half_env_right(eq, Aq, open_phys=True)      # [o, n, L, l, t, t']
+    return np.einsum('onABsp,onABtq->stpq', EL, ER, optimize=True)
 
 
 def expect1(rho, O):

@@ -15,7 +15,8 @@ depend on the gauge.
 Recycled window (Sec. VI.C steps (i)-(iii)):
     A_0 = A_c of the current A; one plain step gives Theta, fu and A~;
     (i)   canonical form of A~: A~_1 = A~ x_legs maps                  (a11)
-    (ii)  gauge fix: A~_1 ~ A_0 x W                                    (a12)
+    (ii)  gauge fix: A~_1 ~ A_0 x W, started from the kappa = 0 block of
+          the leg maps (gauge_start)                                   (a12)
     (iii) renormalised gate: per leg K = P_fu maps W^T (out legs) and
           K = Q_fu^T maps W^T (in legs), kappa*D x D;
           A_k = (g A_{k-1}) x_legs K, k = 1..N_Re, each max-abs normalised (a13)
@@ -30,7 +31,7 @@ from .model import ipepo, apply_pepo
 from .ctmrg import double_layer, ctmrg, init_env
 from .fullupdate import (pretruncation, pretruncated_sites, full_update, assemble,
                          leg_links, leg_mul, LEG)
-from .canonical import canonicalize, gauge_fix
+from .canonical import canonicalize, gauge_fix, polar
 from .observables import measure
 
 
@@ -83,12 +84,30 @@ def recycled_step(A, cell, g, K):
     return out
 
 
+def gauge_start(cell, fu, maps, D):
+    """Starting link matrices of the gauge fix (reading; the paper allows any start).
+
+    For small tau the kappa = 0 block of Theta = g A_0 is A_0 itself up to a
+    scalar, so the kappa = 0 rows of the leg maps P Q_c (out leg) and Q^T Q_c
+    (in leg) of each link estimate the orthogonal W of A~_1 ~ A_0 x W; W starts
+    at the polar factor of their sum.
+    """
+    W0 = {}
+    for t in range(len({tt for (tt, _l) in maps})):
+        for name, (e, side) in leg_links(cell, t).items():
+            P, Q = fu[e]
+            base = P[:D, :] if side == 'out' else Q[:, :D].T
+            W0[e] = W0.get(e, 0.0) + base @ maps[(t, name)]
+    return {e: polar(M) for e, M in W0.items()}
+
+
 def recycle_window(A, cell, cfg, n_re, env=None, g=None):
     """One environment computation followed by n_re applications of the renormalised gate."""
     g = ipepo(cfg.h, cfg.tau) if g is None else g
     At, env, info = fu_step(A, cell, cfg, env, g)
     can1 = canonicalize(At, cell, cfg.canon_tol, cfg.canon_max)
-    W, F, git = gauge_fix(info['A0'], can1['A'], cell, cfg.gauge_tol, cfg.gauge_max)
+    W0 = gauge_start(cell, info['fu'], can1['maps'], cfg.D)
+    W, F, git = gauge_fix(info['A0'], can1['A'], cell, cfg.gauge_tol, cfg.gauge_max, W0=W0)
     K = gate_legs(cell, info['fu'], can1['maps'], W)
     Ak = info['A0']
     for _ in range(n_re):

@@ -1,0 +1,303 @@
+"""ctypes binding of libtnite (include/tnite.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device
+memory (the context workspace, kernel-level operands) comes from PyTorch
+tensors; host arrays are numpy float64.  The library must have been built
+(paper_1411_0391_gb300.build); there is no fallback implementation.
+"""
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_longlong, c_size_t, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_PATH = os.path.join(_HERE, "libtnite.so")
+_LIB = None
+
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE = 0, -1, -2, -3, -4, -5, -6
+TN_CELL_CHECKERBOARD, TN_CELL_SINGLE = 2, 1
+TN_F64 = 0
+(TN_T_STATE, TN_T_CANON, TN_T_LAMBDA, TN_T_THETA, TN_T_PRE_P, TN_T_PRE_Q, TN_T_DOUBLE,
+ TN_T_BOND_ENV, TN_T_FU_P, TN_T_FU_Q, TN_T_GAUGE_W, TN_T_GATE_K, TN_T_PEPO) = range(13)
+
+
+class tn_config(ctypes.Structure):
+    _fields_ = [("D", c_int), ("chi", c_int), ("cell", c_int), ("precision", c_int)]
+
+
+class tn_ctm_report(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("converged", c_int), ("delta", c_double)]
+
+
+class tn_step_report(ctypes.Structure):
+    _fields_ = [("canon_iters", c_int), ("ctm_iterations", c_int), ("ctm_delta", c_double),
+                ("als_iters", c_int * 8), ("als_cost", c_double * 8)]
+
+
+class tn_evolve_opts(ctypes.Structure):
+    _fields_ = [("recycle", c_int), ("n_re", c_int), ("ctm_tol", c_double), ("ctm_max", c_int)]
+
+
+class tn_evolve_report(ctypes.Structure):
+    _fields_ = [("steps", c_int), ("env_computations", c_int), ("ctm_iterations", c_int),
+                ("ctm_moves", c_int), ("nonconverged", c_int), ("last_fidelity", c_double)]
+
+
+class tn_observables(ctypes.Structure):
+    _fields_ = [("e_site", c_double), ("e_link", c_double), ("mx", c_double * 2), ("mz", c_double * 2),
+                ("zz", c_double * 4)]
+
+
+_DP = POINTER(c_double)
+_SIGS = {
+    "tn_launch_count": (ctypes.c_ulonglong, []),
+    "tn_workspace_bytes": (c_size_t, [POINTER(tn_config)]),
+    "tn_create": (c_int, [POINTER(c_void_p), POINTER(tn_config), c_void_p, c_size_t, c_void_p]),
+    "tn_destroy": (None, [c_void_p]),
+    "tn_strerror": (ctypes.c_char_p, [c_int]),
+    "tn_set_hamiltonian": (c_int, [c_void_p, c_double, c_double]),
+    "tn_set_time_step": (c_int, [c_void_p, c_double]),
+    "tn_set_state": (c_int, [c_void_p, _DP, c_size_t]),
+    "tn_get_state": (c_int, [c_void_p, _DP, c_size_t]),
+    "tn_build_double_layer": (c_int, [c_void_p]),
+    "tn_set_network": (c_int, [c_void_p, _DP, c_int, _DP]),
+    "tn_reset_env": (c_int, [c_void_p]),
+    "tn_ctmrg": (c_int, [c_void_p, c_double, c_int, POINTER(tn_ctm_report)]),
+    "tn_ctmrg_moves": (c_int, [c_void_p, c_int]),
+    "tn_env_size": (c_size_t, [c_void_p]),
+    "tn_get_env": (c_int, [c_void_p, _DP, c_size_t]),
+    "tn_set_env": (c_int, [c_void_p, _DP, c_size_t]),
+    "tn_corner_spectra": (c_int, [c_void_p, _DP, c_size_t]),
+    "tn_site_scalars": (c_int, [c_void_p, c_int, _DP, _DP]),
+    "tn_step_prepare": (c_int, [c_void_p, POINTER(tn_step_report)]),
+    "tn_step_update": (c_int, [c_void_p, POINTER(tn_step_report)]),
+    "tn_fu_step": (c_int, [c_void_p, c_double, c_int, POINTER(tn_step_report)]),
+    "tn_recycle": (c_int, [c_void_p, c_int, _DP]),
+    "tn_evolve": (c_int, [c_void_p, c_int, POINTER(tn_evolve_opts), POINTER(tn_evolve_report)]),
+    "tn_measure": (c_int, [c_void_p, POINTER(tn_observables)]),
+    "tn_get_tensor": (c_int, [c_void_p, c_int, c_int, _DP, c_size_t]),
+    "tn_gemm_f64": (c_int, [c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_longlong,
+                            c_void_p, c_int, c_longlong, c_double, c_void_p, c_int, c_longlong, c_int, c_void_p]),
+    "tn_permute_f64": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_int), POINTER(c_int), c_void_p]),
+    "tn_svd_small": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tn_eigh_small": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "tn_truncated_svd": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """Load libtnite.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_PATH):
+            raise RuntimeError("libtnite.so is missing: build it with paper_1411_0391_gb300.build.build()")
+        L = ctypes.CDLL(_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class TnError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().tn_strerror(status).decode()
+        super().__init__("%s: %s (%d)" % (where, msg, status))
+        self.status = status
+
+
+def _check(status, where, allow_noconv=False):
+    if status == TN_OK or (allow_noconv and status == TN_ENOCONV):
+        return status
+    raise TnError(status, where)
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream_ptr(stream):
+    return c_void_p(0 if stream is None else stream.cuda_stream)
+
+
+def tn_launch_count():
+    return int(lib().tn_launch_count())
+
+
+# ---- kernel-level entry points (torch device tensors) ------------------------
+
+def tn_gemm_f64(transA, transB, m, n, k, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC,
+                batch, stream=None):
+    _check(lib().tn_gemm_f64(int(transA), int(transB), m, n, k, alpha, c_void_p(A.data_ptr()), lda, strideA,
+                             c_void_p(B.data_ptr()), ldb, strideB, beta, c_void_p(C.data_ptr()), ldc, strideC,
+                             batch, _stream_ptr(stream)), "tn_gemm_f64")
+
+
+def tn_permute_f64(inp, out, dims, perm, stream=None):
+    r = len(dims)
+    _check(lib().tn_permute_f64(c_void_p(inp.data_ptr()), c_void_p(out.data_ptr()), r, (c_int * r)(*dims),
+                                (c_int * r)(*perm), _stream_ptr(stream)), "tn_permute_f64")
+
+
+def tn_svd_small(A, m, n, batch, U, S, V, stream=None):
+    _check(lib().tn_svd_small(c_void_p(A.data_ptr()), m, n, batch, c_void_p(U.data_ptr()), c_void_p(S.data_ptr()),
+                              c_void_p(V.data_ptr()), _stream_ptr(stream)), "tn_svd_small")
+
+
+def tn_eigh_small(A, n, batch, W, V, stream=None):
+    _check(lib().tn_eigh_small(c_void_p(A.data_ptr()), n, batch, c_void_p(W.data_ptr()), c_void_p(V.data_ptr()),
+                               _stream_ptr(stream)), "tn_eigh_small")
+
+
+def tn_truncated_svd(ctx, M, m, k, U, S, V, warm=None):
+    return _check(lib().tn_truncated_svd(ctx.handle, c_void_p(M.data_ptr()), m, k, c_void_p(U.data_ptr()),
+                                         c_void_p(S.data_ptr()), c_void_p(V.data_ptr()),
+                                         c_void_p(0 if warm is None else warm.data_ptr())),
+                  "tn_truncated_svd", allow_noconv=True)
+
+
+# ---- context -----------------------------------------------------------------
+
+class Context:
+    """One tnite context: its device workspace is a torch uint8 tensor on `device`."""
+
+    def __init__(self, D, chi, cell=TN_CELL_CHECKERBOARD, device="cuda:0", stream=None):
+        import torch
+        self.cfg = tn_config(D, chi, cell, TN_F64)
+        nbytes = lib().tn_workspace_bytes(byref(self.cfg))
+        if nbytes == 0:
+            raise TnError(TN_EINVAL, "tn_workspace_bytes")
+        self.device = torch.device(device)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = c_void_p()
+        _check(lib().tn_create(byref(h), byref(self.cfg), c_void_p(self.workspace.data_ptr()), nbytes,
+                               c_void_p(self.stream.cuda_stream)), "tn_create")
+        self.handle = h
+        self.D, self.chi = D, chi
+        self.n_tensors = 2 if cell == TN_CELL_CHECKERBOARD else 1
+        self.n_links = 2 * self.n_tensors
+        self.n_sites = 4 if cell == TN_CELL_CHECKERBOARD else 1
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # problem definition
+    def tn_set_hamiltonian(self, J, h):
+        _check(lib().tn_set_hamiltonian(self.handle, J, h), "tn_set_hamiltonian")
+
+    def tn_set_time_step(self, tau):
+        _check(lib().tn_set_time_step(self.handle, tau), "tn_set_time_step")
+
+    def tn_set_state(self, tensors):
+        buf = _f64(np.concatenate([np.ravel(t) for t in tensors]))
+        _check(lib().tn_set_state(self.handle, _dp(buf), buf.size), "tn_set_state")
+
+    def tn_get_state(self):
+        per = 2 * self.D ** 4
+        buf = np.empty(per * self.n_tensors)
+        _check(lib().tn_get_state(self.handle, _dp(buf), buf.size), "tn_get_state")
+        return [buf[i * per:(i + 1) * per].reshape(2, *(self.D,) * 4).copy() for i in range(self.n_tensors)]
+
+    # environment
+    def tn_build_double_layer(self):
+        _check(lib().tn_build_double_layer(self.handle), "tn_build_double_layer")
+
+    def tn_set_network(self, tensors, boundary=None):
+        a = _f64(np.concatenate([np.ravel(t) for t in tensors]))
+        leg = int(tensors[0].shape[0])
+        b = None if boundary is None else _f64(boundary)
+        _check(lib().tn_set_network(self.handle, _dp(a), leg, None if b is None else _dp(b)), "tn_set_network")
+        self.leg = leg
+
+    def tn_reset_env(self):
+        _check(lib().tn_reset_env(self.handle), "tn_reset_env")
+
+    def tn_ctmrg(self, tol, max_iter):
+        rep = tn_ctm_report()
+        s = _check(lib().tn_ctmrg(self.handle, tol, max_iter, byref(rep)), "tn_ctmrg", allow_noconv=True)
+        return dict(iterations=rep.iterations, converged=bool(rep.converged), delta=rep.delta, status=s)
+
+    def tn_ctmrg_moves(self, n):
+        _check(lib().tn_ctmrg_moves(self.handle, n), "tn_ctmrg_moves")
+
+    def tn_get_env(self):
+        n = lib().tn_env_size(self.handle)
+        buf = np.empty(n)
+        _check(lib().tn_get_env(self.handle, _dp(buf), n), "tn_get_env")
+        return buf
+
+    def tn_set_env(self, buf):
+        buf = _f64(buf)
+        _check(lib().tn_set_env(self.handle, _dp(buf), buf.size), "tn_set_env")
+
+    def tn_corner_spectra(self):
+        buf = np.empty(self.n_sites * 4 * self.chi)
+        _check(lib().tn_corner_spectra(self.handle, _dp(buf), buf.size), "tn_corner_spectra")
+        return buf.reshape(self.n_sites, 4, self.chi)
+
+    def tn_site_scalars(self, site, a=None):
+        out = np.empty(4)
+        ap = None if a is None else _f64(a)
+        _check(lib().tn_site_scalars(self.handle, site, None if ap is None else _dp(ap), _dp(out)), "tn_site_scalars")
+        return out
+
+    # imaginary-time step
+    @staticmethod
+    def _step(rep):
+        return dict(canon_iters=rep.canon_iters, ctm_iterations=rep.ctm_iterations, ctm_delta=rep.ctm_delta,
+                    als_iters=list(rep.als_iters), als_cost=list(rep.als_cost))
+
+    def tn_step_prepare(self):
+        rep = tn_step_report()
+        _check(lib().tn_step_prepare(self.handle, byref(rep)), "tn_step_prepare")
+        return self._step(rep)
+
+    def tn_step_update(self):
+        rep = tn_step_report()
+        _check(lib().tn_step_update(self.handle, byref(rep)), "tn_step_update")
+        return self._step(rep)
+
+    def tn_fu_step(self, ctm_tol, ctm_max):
+        rep = tn_step_report()
+        _check(lib().tn_fu_step(self.handle, ctm_tol, ctm_max, byref(rep)), "tn_fu_step", allow_noconv=True)
+        return self._step(rep)
+
+    def tn_recycle(self, n_re):
+        F = c_double(0.0)
+        _check(lib().tn_recycle(self.handle, n_re, byref(F)), "tn_recycle")
+        return F.value
+
+    def tn_evolve(self, n_steps, recycle=False, n_re=1, ctm_tol=1e-10, ctm_max=500):
+        o = tn_evolve_opts(int(recycle), n_re, ctm_tol, ctm_max)
+        rep = tn_evolve_report()
+        _check(lib().tn_evolve(self.handle, n_steps, byref(o), byref(rep)), "tn_evolve")
+        return dict(steps=rep.steps, env_computations=rep.env_computations, ctm_iterations=rep.ctm_iterations,
+                    ctm_moves=rep.ctm_moves, nonconverged=rep.nonconverged, last_fidelity=rep.last_fidelity)
+
+    def tn_measure(self):
+        o = tn_observables()
+        _check(lib().tn_measure(self.handle, byref(o)), "tn_measure")
+        nt, nl = self.n_tensors, self.n_links
+        return dict(e_site=o.e_site, e_link=o.e_link, mx=list(o.mx)[:nt], mz=list(o.mz)[:nt], zz=list(o.zz)[:nl])
+
+    def tn_get_tensor(self, which, index, shape):
+        buf = np.empty(int(np.prod(shape)))
+        _check(lib().tn_get_tensor(self.handle, which, index, _dp(buf), buf.size), "tn_get_tensor")
+        return buf.reshape(shape)

@@ -1,0 +1,257 @@
+// Dense building blocks in double precision: batched strided GEMM, tensor
+// permutation and small element-wise kernels.
+//
+// GB300 executes FP64 on the SIMT pipe only (no FP64 tensor-core path), at a
+// rate far below its memory bandwidth, so the GEMM is a register-tiled SIMT
+// kernel whose only job is to keep the FP64 units busy: 64x64 output tiles,
+// 16-deep k slices staged in shared memory, 4x4 outputs per thread.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tn {
+
+constexpr int GT = 64;     // tile edge
+constexpr int GK = 16;     // k slice
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double alpha,
+        const double* __restrict__ A, int lda, long long sA,
+        const double* __restrict__ B, int ldb, long long sB, double beta,
+        double* __restrict__ C, int ldc, long long sC)
+{
+    __shared__ double As[GK][GT + 1];
+    __shared__ double Bs[GK][GT + 1];
+    const int b = blockIdx.z;
+    A += b * sA; B += b * sB; C += b * sC;
+    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    for (int k0 = 0; k0 < k; k0 += GK) {
+        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+            int r, kk;
+            if (TA) { r = e % GT; kk = e / GT; } else { kk = e % GK; r = e / GK; }
+            int gr = row0 + r, gk = k0 + kk;
+            double v = 0.0;
+            if (gr < m && gk < k) v = TA ? A[(long long)gk * lda + gr] : A[(long long)gr * lda + gk];
+            As[kk][r] = v;
+        }
+        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+            int c, kk;
+            if (TB) { kk = e % GK; c = e / GK; } else { c = e % GT; kk = e / GT; }
+            int gc = col0 + c, gk = k0 + kk;
+            double v = 0.0;
+            if (gc < n && gk < k) v = TB ? B[(long long)gc * ldb + gk] : B[(long long)gk * ldb + gc];
+            Bs[kk][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int r = row0 + ty + 16 * i;
+        if (r >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int c = col0 + tx + 16 * j;
+            if (c >= n) continue;
+            double* dst = C + (long long)r * ldc + c;
+            *dst = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*dst);
+        }
+    }
+}
+
+int gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
+         const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
+         double beta, double* C, int ldc, long long sC, int batch)
+{
+    if (m <= 0 || n <= 0 || batch <= 0) return TN_OK;
+    if (k <= 0) {   // C = beta C
+        if (beta == 1.0) return TN_OK;
+        for (int b = 0; b < batch; ++b)
+            TN_TRY(scale_rows(st, C + b * sC, m, n, ldc, beta));
+        return TN_OK;
+    }
+    if (batch > 65535) return TN_EINVAL;
+    dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, batch);
+    if (grid.y > 65535) return TN_EINVAL;
+    if (!ta && !tb) dgemm_kernel<false, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else if (ta && !tb) dgemm_kernel<true, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else if (!ta && tb) dgemm_kernel<false, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else dgemm_kernel<true, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// permutation: output axis j is input axis perm[j]
+// ---------------------------------------------------------------------------
+struct PermArgs {
+    int rank;
+    long long out_dim[8];
+    long long in_stride_of_out[8];   // input stride of output axis j
+};
+
+__global__ void permute_kernel(const double* __restrict__ in, double* __restrict__ out,
+                               long long total, PermArgs a)
+{
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
+        long long rem = o, src = 0;
+        for (int j = a.rank - 1; j >= 0; --j) {
+            long long idx = rem % a.out_dim[j];
+            rem /= a.out_dim[j];
+            src += idx * a.in_stride_of_out[j];
+        }
+        out[o] = in[src];
+    }
+}
+
+int permute(cudaStream_t st, const double* in, double* out, int rank, const int* dims, const int* perm)
+{
+    if (rank < 1 || rank > 8) return TN_EINVAL;
+    long long stride[8];
+    long long total = 1;
+    for (int i = rank - 1; i >= 0; --i) { stride[i] = total; total *= dims[i]; }
+    PermArgs a;
+    a.rank = rank;
+    bool ident = true;
+    for (int j = 0; j < rank; ++j) {
+        if (perm[j] < 0 || perm[j] >= rank) return TN_EINVAL;
+        a.out_dim[j] = dims[perm[j]];
+        a.in_stride_of_out[j] = stride[perm[j]];
+        if (perm[j] != j) ident = false;
+    }
+    if (total == 0) return TN_OK;
+    if (ident) { TN_CUDA(cudaMemcpyAsync(out, in, total * sizeof(double), cudaMemcpyDeviceToDevice, st)); return TN_OK; }
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    permute_kernel<<<(int)blocks, 256, 0, st>>>(in, out, total, a);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// element-wise helpers
+// ---------------------------------------------------------------------------
+__global__ void scale_rows_kernel(double* C, int m, int n, int ldc, double s)
+{
+    long long total = (long long)m * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e / n), c = (int)(e % n);
+        C[(long long)r * ldc + c] *= s;
+    }
+}
+
+int scale_rows(cudaStream_t st, double* C, int m, int n, int ldc, double s)
+{
+    long long total = (long long)m * n;
+    if (total == 0) return TN_OK;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+    scale_rows_kernel<<<blocks, 256, 0, st>>>(C, m, n, ldc, s);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// Each block normalises one tensor of a batch by its largest |entry| (no-op
+// if the tensor is zero).  Tensors are small (<= a few 10^5 entries).
+__global__ void __launch_bounds__(1024) normalize_maxabs_kernel(double* x, long long n, long long stride)
+{
+    double* p = x + blockIdx.x * stride;
+    __shared__ double red[32];
+    double m = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(p[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    double mx = red[0];
+    if (mx == 0.0) return;
+    double inv = 1.0 / mx;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) p[i] *= inv;
+}
+
+int normalize_maxabs(cudaStream_t st, double* x, long long n, int batch, long long stride)
+{
+    if (batch <= 0 || n <= 0) return TN_OK;
+    normalize_maxabs_kernel<<<batch, 1024, 0, st>>>(x, n, stride);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+__global__ void fill_kernel(double* x, long long n, double v)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) x[i] = v;
+}
+
+int fill(cudaStream_t st, double* x, long long n, double v)
+{
+    if (n <= 0) return TN_OK;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    fill_kernel<<<blocks, 256, 0, st>>>(x, n, v);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// Counter-based uniform numbers in [-1, 1): splitmix64 of (seed, index).
+__global__ void hash_fill_kernel(double* x, long long n, unsigned long long seed)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z = z ^ (z >> 31);
+        x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+}
+
+int hash_fill(cudaStream_t st, double* x, long long n, unsigned long long seed)
+{
+    if (n <= 0) return TN_OK;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    hash_fill_kernel<<<blocks, 256, 0, st>>>(x, n, seed);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// y[i] = a * x[i] + b * y[i]
+__global__ void axpby_kernel(double* y, const double* x, long long n, double a, double b)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) y[i] = a * x[i] + b * y[i];
+}
+
+int axpby(cudaStream_t st, double* y, const double* x, long long n, double a, double b)
+{
+    if (n <= 0) return TN_OK;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    axpby_kernel<<<blocks, 256, 0, st>>>(y, x, n, a, b);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+}  // namespace tn

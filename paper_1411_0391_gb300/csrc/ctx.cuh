@@ -1,0 +1,96 @@
+// Context of the tnite library: configuration, device buffers (all carved from
+// the caller's workspace) and the frame bookkeeping of the CTMRG.
+#pragma once
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tn {
+
+constexpr int MAXT = 2;        // tensor ids per cell
+constexpr int MAXL = 4;        // link types per cell
+constexpr int MAXS = 4;        // sites per cell
+
+// Environment of one site: C1..C4 then T1..T4 (clockwise in/out legs).
+struct Env { double* C[4]; double* T[4]; };
+
+// A view of the network after r counter-clockwise rotations: cell geometry,
+// which stored environment plays which role, and which rotated double layer
+// sits on each tensor id.  Rotations only relabel pointers.
+struct Frame {
+    int Lx, Ly, rot;
+    int pat[4][4];             // pat[y][x] = tensor id
+    Env env[MAXS];             // env[y*Lx + x]
+    int tid(int x, int y) const { x %= Lx; if (x < 0) x += Lx; y %= Ly; if (y < 0) y += Ly; return pat[y][x]; }
+    Env& e(int x, int y) { x %= Lx; if (x < 0) x += Lx; y %= Ly; if (y < 0) y += Ly; return env[y * Lx + x]; }
+    Frame rotated() const;
+};
+
+struct Ctx {
+    tn_config cfg;
+    cudaStream_t st = nullptr;
+    Arena ar;
+    size_t scratch_base = 0;
+
+    int nt = 0, nl = 0, Lx = 0, Ly = 0, nsites = 0;
+    int pat[4][4];
+    int D = 0, chi = 0, kD = 0, leg = 0;   // leg: dimension of a double-layer leg
+    double J = 1.0, h = 0.0, tau = 0.0;
+    bool have_state = false, have_network = false, have_pepo = false, prepared = false, updated = false;
+
+    // state and step tensors
+    double* A[MAXT];
+    double* Ac[MAXT];          // weighted canonical form (a11)
+    double* A0[MAXT];          // recycling reference
+    double* A1[MAXT];          // pre-truncated sites / canonical form of the updated state
+    double* lam[MAXL];
+    double* cmaps[MAXT][4];    // canonical leg maps of the last canonicalisation (D x D)
+    double* g = nullptr;       // iPEPO d*d*16
+    double* Theta[MAXT];
+    double* preP[MAXL];
+    double* preQ[MAXL];
+    double* N4[MAXL];
+    double* fuP[MAXL];
+    double* fuQ[MAXL];
+    double* W[MAXL];
+    double* K[MAXT][4];
+    // network and environment
+    double* a[4][MAXT];        // double layer per rotation and tensor id, leg^4
+    double* ab[4][MAXT][4];    // a transposed for enlarged corner type c (UL, UR, LR, LL)
+    double* aT4[4][MAXT];      // a[l][d][r][u] for the edge renormalisation
+    double* boundary = nullptr;
+    double* envbuf = nullptr;
+    Env env0[MAXS];            // environment storage in the unrotated frame
+    double* warmV[4][4][4];    // projector right vectors (rotation, x, y) for warm starts
+    bool warm_ok[4][4][4];
+    double* Pup[4];            // projectors of the current column, per y
+    double* Plo[4];
+    double* dscratch = nullptr;   // small device scratch (reports)
+    double* hbuf = nullptr;
+
+    long long ctm_moves = 0;
+    std::vector<double> prev_spectra;
+
+    int N() const { return chi * leg; }
+    size_t env_size() const { return (size_t)nsites * (4 * (size_t)chi * chi + 4 * (size_t)chi * chi * leg); }
+    Frame frame0();
+};
+
+// ctmrg.cu
+int ctx_build_network_views(Ctx& c);                  // a -> rotations, ab, aT4
+int ctx_reset_env(Ctx& c);
+int ctmrg_move(Ctx& c, Frame& f);                      // one left move in frame f
+int ctmrg_iterations(Ctx& c, double tol, int max_iter, tn_ctm_report* rep);
+int ctmrg_moves(Ctx& c, int n);
+int corner_spectra(Ctx& c, std::vector<double>& out);
+int site_scalars(Ctx& c, int site, const double* d_a, double out[4]);
+
+// step.cu
+int build_pepo(Ctx& c);
+int build_double_layers(Ctx& c, double* const* sites, int Dsite);
+int canonicalize(Ctx& c, double* const* A, double* const* Aout, int* iters, bool keep_maps);
+int step_prepare(Ctx& c, tn_step_report* rep);
+int step_update(Ctx& c, tn_step_report* rep);
+int recycle(Ctx& c, int n_re, double* F);
+int measure(Ctx& c, tn_observables* obs);
+
+}  // namespace tn

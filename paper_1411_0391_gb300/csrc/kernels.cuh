@@ -1,0 +1,36 @@
+// Internal (non-exported) entry points of the tnite library.
+#pragma once
+#include "common.cuh"
+
+namespace tn {
+
+struct TsvdStats { int iterations = 0; };
+
+// basic.cu
+int gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
+         const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
+         double beta, double* C, int ldc, long long sC, int batch);
+int permute(cudaStream_t st, const double* in, double* out, int rank, const int* dims, const int* perm);
+int scale_rows(cudaStream_t st, double* C, int m, int n, int ldc, double s);
+int normalize_maxabs(cudaStream_t st, double* x, long long n, int batch, long long stride);
+int fill(cudaStream_t st, double* x, long long n, double v);
+int hash_fill(cudaStream_t st, double* x, long long n, unsigned long long seed);
+int axpby(cudaStream_t st, double* y, const double* x, long long n, double a, double b);
+
+// linalg.cu
+int svd_small(cudaStream_t st, const double* A, int m, int n, int batch, double* U, double* S, double* V);
+int eigh_small(cudaStream_t st, const double* A, int n, int batch, double* W, double* V);
+int chol_inv(cudaStream_t st, const double* G, int n, double c_shift, double* X);
+int sign_fix_cols(cudaStream_t st, double* U, double* V, int rows, int vrows, int cols);
+int orth(cudaStream_t st, Arena& ar, double* Y, int rows, int cols);
+int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
+                  double* U, double* S, double* V, const double* warm, TsvdStats* stats);
+
+// contract.cu: C = alpha * A.B (+ beta C when no output permutation is needed),
+// einsum-style labels "ab,bcm->acm" (no traces, no batch labels).
+int contract(cudaStream_t st, Arena& ar, const char* spec, const DT& A, const DT& B, const DT& C,
+             double alpha = 1.0, double beta = 0.0);
+// out = in with axes permuted by a label spec "abcd->cabd"
+int permute_spec(cudaStream_t st, const char* spec, const DT& in, const DT& out);
+
+}  // namespace tn

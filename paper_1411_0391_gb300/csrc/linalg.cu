@@ -1,0 +1,260 @@
+// Small dense factorisations (one thread block per matrix) and the truncated
+// SVD used for the CTMRG projectors.
+//
+// Truncated SVD of an m x m matrix M (top k triplets):
+//   m <= SMALL_MAX: one-sided Jacobi SVD of M itself;
+//   otherwise subspace iteration with kk = k + oversampling columns:
+//     Y = orth(M Om), Z = orth(M^T Y), B = Y^T M Z = Ub Sb Vb^T (Jacobi),
+//     repeated with Om = Z until the top-k Ritz values stop changing;
+//     U = Y Ub, V = Z Vb.  orth() is the shifted Cholesky-QR3 of Fukaya et al.
+//     (shifted CholQR, then CholQR twice): all products run as GEMMs over the
+//     whole GPU, only the kk x kk Cholesky runs in one block.
+// The sign rule (largest |entry| of each column of U positive) is applied to
+// the final m-long vectors.
+#include <algorithm>
+#include <cmath>
+#include "common.cuh"
+#include "kernels.cuh"
+#include "smallla.cuh"
+
+namespace tn {
+
+// ---------------------------------------------------------------------------
+// batched small SVD
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) svd_small_kernel(const double* __restrict__ Ain, int m, int n,
+        double* __restrict__ Uout, double* __restrict__ Sout, double* __restrict__ Vout, int max_sweeps)
+{
+    extern __shared__ double sm[];
+    double* U = sm;                 // m*n column-major
+    double* V = U + m * n;          // n*n column-major
+    double* key = V + n * n;        // n
+    __shared__ int flag;
+    (void)max_sweeps;
+    dev_svd(Ain + (size_t)blockIdx.x * m * n, m, n, U, Sout + (size_t)blockIdx.x * n, V, key, &flag);
+    double* Uo = Uout + (size_t)blockIdx.x * m * n;
+    double* Vo = Vout + (size_t)blockIdx.x * n * n;
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) Uo[e] = U[(e % n) * m + e / n];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Vo[e] = V[(e % n) * n + e / n];
+}
+
+static size_t svd_smem(int m, int n) { return sizeof(double) * ((size_t)m * n + (size_t)n * n + n) + 64; }
+
+int svd_small(cudaStream_t st, const double* A, int m, int n, int batch, double* U, double* S, double* V)
+{
+    if (n < 1 || m < n || m > SMALL_MAX || batch < 1) return TN_EINVAL;
+    size_t smem = svd_smem(m, n);
+    static bool attr = false;
+    if (!attr) {
+        TN_CUDA(cudaFuncSetAttribute(svd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)svd_smem(SMALL_MAX, SMALL_MAX)));
+        attr = true;
+    }
+    svd_small_kernel<<<batch, 512, smem, st>>>(A, m, n, U, S, V, 60);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched symmetric eigendecomposition, eigenvalues ascending, sign rule on
+// the eigenvectors
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) eigh_small_kernel(const double* __restrict__ Ain, int n,
+        double* __restrict__ Wout, double* __restrict__ Vout, int max_sweeps)
+{
+    extern __shared__ double sm[];
+    double* A = sm;                   // n*n
+    double* V = A + n * n;            // n*n column-major
+    double* cs = V + n * n;           // 2*(n/2+1)
+    int* pq = (int*)(cs + 2 * (n / 2 + 1));
+    __shared__ double red[32];
+    (void)max_sweeps;
+    dev_eigh(Ain + (size_t)blockIdx.x * n * n, n, A, Wout + (size_t)blockIdx.x * n, V, cs, pq, red);
+    double* Vo = Vout + (size_t)blockIdx.x * n * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Vo[e] = V[(e % n) * n + e / n];
+}
+
+static size_t eigh_smem(int n) { return sizeof(double) * (2 * (size_t)n * n + 2 * (n / 2 + 1)) + sizeof(int) * 2 * (n / 2 + 1) + 64; }
+
+int eigh_small(cudaStream_t st, const double* A, int n, int batch, double* W, double* V)
+{
+    if (n < 1 || n > SMALL_MAX || batch < 1) return TN_EINVAL;
+    static bool attr = false;
+    if (!attr) {
+        TN_CUDA(cudaFuncSetAttribute(eigh_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)eigh_smem(SMALL_MAX)));
+        attr = true;
+    }
+    eigh_small_kernel<<<batch, 512, eigh_smem(n), st>>>(A, n, W, V, 60);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky inverse for the orthonormalisation; shift = c_shift * u * tr(G)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) chol_inv_kernel(const double* __restrict__ Gin, int n,
+        double c_shift, double* __restrict__ Xout)
+{
+    extern __shared__ double sm[];
+    double* G = sm;              // n*n
+    double* X = G + n * n;       // n*n
+    int* dead = (int*)(X + n * n);
+    __shared__ double red[32];
+    double tr = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        G[e] = Gin[e];
+        if (e % n == e / n) tr += Gin[e];
+    }
+    tr = block_sum(tr, red);
+    const double shift = c_shift * 1.1102230246251565e-16 * tr;
+    blk_chol_inv(G, n, shift, 1e-26, X, dead, red);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xout[e] = X[e];
+}
+
+static size_t chol_smem(int n) { return sizeof(double) * 2 * (size_t)n * n + sizeof(int) * n + 64; }
+
+int chol_inv(cudaStream_t st, const double* G, int n, double c_shift, double* X)
+{
+    if (n < 1 || n > SMALL_MAX) return TN_EINVAL;
+    static bool attr = false;
+    if (!attr) {
+        TN_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)chol_smem(SMALL_MAX)));
+        attr = true;
+    }
+    chol_inv_kernel<<<1, 512, chol_smem(n), st>>>(G, n, c_shift, X);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// Sign rule on the columns of row-major U (rows x cols), flipping V too.
+__global__ void sign_fix_cols_kernel(double* U, double* V, int rows, int vrows, int cols)
+{
+    const int j = blockIdx.x;
+    __shared__ double red[32];
+    __shared__ int firsts[32];
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) mx = fmax(mx, fabs(U[(size_t)i * cols + j]));
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        red[0] = m;
+    }
+    __syncthreads();
+    mx = red[0];
+    if (mx == 0.0) return;
+    const double thr = mx * (1.0 - 1e-10);
+    int first = rows;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x)
+        if (fabs(U[(size_t)i * cols + j]) >= thr) { first = i; break; }
+    for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+    if ((threadIdx.x & 31) == 0) firsts[threadIdx.x >> 5] = first;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int f = rows;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f = min(f, firsts[w]);
+        firsts[0] = f;
+    }
+    __syncthreads();
+    if (U[(size_t)firsts[0] * cols + j] >= 0.0) return;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) U[(size_t)i * cols + j] = -U[(size_t)i * cols + j];
+    if (V) for (int i = threadIdx.x; i < vrows; i += blockDim.x) V[(size_t)i * cols + j] = -V[(size_t)i * cols + j];
+}
+
+int sign_fix_cols(cudaStream_t st, double* U, double* V, int rows, int vrows, int cols)
+{
+    if (cols <= 0) return TN_OK;
+    sign_fix_cols_kernel<<<cols, 256, 0, st>>>(U, V, rows, vrows, cols);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// orthonormalisation (shifted CholeskyQR3) of Y (rows x cols, row-major)
+// ---------------------------------------------------------------------------
+int orth(cudaStream_t st, Arena& ar, double* Y, int rows, int cols)
+{
+    size_t mk = ar.mark();
+    double* G = ar.take((size_t)cols * cols);
+    double* X = ar.take((size_t)cols * cols);
+    double* T = ar.take((size_t)rows * cols);
+    if (!G || !X || !T) { ar.release(mk); return TN_ENOMEM; }
+    const double c_first = 11.0 * ((double)rows * cols + (double)cols * (cols + 1));
+    for (int pass = 0; pass < 3; ++pass) {
+        TN_TRY(gemm(st, true, false, cols, cols, rows, 1.0, Y, cols, 0, Y, cols, 0, 0.0, G, cols, 0, 1));
+        TN_TRY(chol_inv(st, G, cols, pass == 0 ? c_first : 0.0, X));
+        TN_TRY(gemm(st, false, false, rows, cols, cols, 1.0, Y, cols, 0, X, cols, 0, 0.0, T, cols, 0, 1));
+        TN_CUDA(cudaMemcpyAsync(Y, T, sizeof(double) * rows * cols, cudaMemcpyDeviceToDevice, st));
+    }
+    ar.release(mk);
+    return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// truncated SVD
+// ---------------------------------------------------------------------------
+int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
+                  double* U, double* S, double* V, const double* warm, TsvdStats* stats)
+{
+    if (k < 1 || k > m) return TN_EINVAL;
+    size_t mk = ar.mark();
+    if (m <= SMALL_MAX) {
+        double* Uf = ar.take((size_t)m * m);
+        double* Sf = ar.take(m);
+        double* Vf = ar.take((size_t)m * m);
+        if (!Uf || !Sf || !Vf) { ar.release(mk); return TN_ENOMEM; }
+        TN_TRY(svd_small(st, M, m, m, 1, Uf, Sf, Vf));
+        TN_CUDA(cudaMemcpy2DAsync(U, k * sizeof(double), Uf, m * sizeof(double), k * sizeof(double), m, cudaMemcpyDeviceToDevice, st));
+        TN_CUDA(cudaMemcpy2DAsync(V, k * sizeof(double), Vf, m * sizeof(double), k * sizeof(double), m, cudaMemcpyDeviceToDevice, st));
+        TN_CUDA(cudaMemcpyAsync(S, Sf, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (stats) { stats->iterations = 0; }
+        ar.release(mk);
+        return TN_OK;
+    }
+    int kk = std::min(m, std::min(SMALL_MAX, k + std::max(8, k / 4)));
+    double* Om = ar.take((size_t)m * kk);
+    double* Y = ar.take((size_t)m * kk);
+    double* Z = ar.take((size_t)m * kk);
+    double* T = ar.take((size_t)m * kk);
+    double* B = ar.take((size_t)kk * kk);
+    double* Ub = ar.take((size_t)kk * kk);
+    double* Sb = ar.take(kk);
+    double* Vb = ar.take((size_t)kk * kk);
+    if (!Om || !Y || !Z || !T || !B || !Ub || !Sb || !Vb) { ar.release(mk); return TN_ENOMEM; }
+    TN_TRY(hash_fill(st, Om, (long long)m * kk, 0x5eed0000ull + (unsigned long long)m * 131 + k));
+    if (warm)
+        TN_CUDA(cudaMemcpy2DAsync(Om, kk * sizeof(double), warm, k * sizeof(double), k * sizeof(double), m, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> prev(kk, -1.0), cur(kk);
+    const int max_it = 16;
+    int it = 0;
+    for (; it < max_it; ++it) {
+        TN_TRY(gemm(st, false, false, m, kk, m, 1.0, M, m, 0, Om, kk, 0, 0.0, Y, kk, 0, 1));
+        TN_TRY(orth(st, ar, Y, m, kk));
+        TN_TRY(gemm(st, true, false, m, kk, m, 1.0, M, m, 0, Y, kk, 0, 0.0, Z, kk, 0, 1));
+        TN_TRY(orth(st, ar, Z, m, kk));
+        TN_TRY(gemm(st, false, false, m, kk, m, 1.0, M, m, 0, Z, kk, 0, 0.0, T, kk, 0, 1));
+        TN_TRY(gemm(st, true, false, kk, kk, m, 1.0, Y, kk, 0, T, kk, 0, 0.0, B, kk, 0, 1));
+        TN_TRY(svd_small(st, B, kk, kk, 1, Ub, Sb, Vb));
+        TN_CUDA(cudaMemcpyAsync(cur.data(), Sb, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TN_CUDA(cudaStreamSynchronize(st));
+        double dmax = 0.0;
+        for (int i = 0; i < k; ++i) dmax = std::max(dmax, std::fabs(cur[i] - prev[i]));
+        prev = cur;
+        std::swap(Om, Z);
+        if (it >= 1 && dmax <= 1e-14 * std::max(cur[0], 1e-300)) { ++it; break; }
+    }
+    // after the swap, Om holds the last Z
+    TN_TRY(gemm(st, false, false, m, k, kk, 1.0, Y, kk, 0, Ub, kk, 0, 0.0, U, k, 0, 1));
+    TN_TRY(gemm(st, false, false, m, k, kk, 1.0, Om, kk, 0, Vb, kk, 0, 0.0, V, k, 0, 1));
+    TN_CUDA(cudaMemcpyAsync(S, Sb, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TN_TRY(sign_fix_cols(st, U, V, m, m, k));
+    if (stats) stats->iterations = it;
+    ar.release(mk);
+    return it > max_it ? TN_ENOCONV : TN_OK;
+}
+
+}  // namespace tn

@@ -1,0 +1,135 @@
+"""GPU parity of the CTMRG (rows a2-a6) against the oracle, and the classical-Ising pin on the GPU."""
+import numpy as np
+import pytest
+
+from oracle import classical as K
+from oracle import ctmrg as OC
+from paper_1411_0391_gb300 import _lib as L
+from paper_1411_0391_gb300 import build as B
+from paper_1411_0391_gb300.inputs import random_peps
+from tests.gpu_common import env_to_dict, rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    L.lib()
+
+
+def _gpu_after_moves(A, D, chi, n_moves):
+    ctx = L.Context(D, chi)
+    ctx.tn_set_state(A)
+    ctx.tn_build_double_layer()
+    ctx.tn_reset_env()
+    ctx.tn_ctmrg_moves(n_moves)
+    env = env_to_dict(ctx.tn_get_env(), 2, chi, D * D)
+    return ctx, env
+
+
+def _oracle_after_moves(A, chi, n_moves):
+    cell = OC.checkerboard()
+    a = [OC.double_layer(x) for x in A]
+    st = OC.State(cell, a, OC.init_env(cell, chi, a[0].shape[0]))
+    for _ in range(n_moves):
+        OC.left_move(st, chi)
+        st = st.rotated()
+    for _ in range((4 - n_moves % 4) % 4):
+        st = st.rotated()
+    return st
+
+
+def test_double_layer():
+    A = random_peps(2, 3, instance=1)
+    ctx = L.Context(3, 8)
+    ctx.tn_set_state(A)
+    ctx.tn_build_double_layer()
+    for t in range(2):
+        a = ctx.tn_get_tensor(L.TN_T_DOUBLE, t, (9, 9, 9, 9))
+        np.testing.assert_allclose(a, OC.double_layer(A[t]), rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("D,chi,n_moves", [(2, 6, 1), (2, 6, 4), (2, 8, 8), (3, 16, 4)])
+def test_moves_match_oracle(D, chi, n_moves):
+    """Environment after n directional moves, element by element (sign rule on both sides).
+
+    chi * D^2 = 144 > 112 for (3, 16) exercises the subspace-iteration projector SVD.
+    Tolerance: projector directions with s_i near the 1e-12 s_1 cutoff carry
+    vectors known only to ~eps s_1 / s_i in FP64 (LAPACK and Jacobi alike), so
+    tensors agree to ~1e-8 while the spectra agree to 1e-9 and below.
+    """
+    A = random_peps(2, D, instance=2)
+    ctx, env = _gpu_after_moves(A, D, chi, n_moves)
+    st = _oracle_after_moves(A, chi, n_moves)
+    for site, e in env.items():
+        for name, T in e.items():
+            ref = st.env[site][name]
+            assert rel_err(T, ref) < 1e-7, (site, name, rel_err(T, ref))
+    ctx.close()
+
+
+@pytest.mark.parametrize("D,chi", [(2, 8), (2, 12)])
+def test_converged_corner_spectra(D, chi):
+    A = random_peps(2, D, instance=3)
+    ctx = L.Context(D, chi)
+    ctx.tn_set_state(A)
+    ctx.tn_build_double_layer()
+    ctx.tn_reset_env()
+    rep = ctx.tn_ctmrg(1e-11, 300)
+    sp = ctx.tn_corner_spectra()
+    cell = OC.checkerboard()
+    st, it, d, conv = OC.ctmrg(cell, [OC.double_layer(x) for x in A], chi, 1e-11, 300)
+    ref = OC.corner_spectra(st)
+    for i, (x, y) in enumerate([(0, 0), (1, 0), (0, 1), (1, 1)]):
+        for c in range(4):
+            np.testing.assert_allclose(sp[i, c], ref[(x, y, 'C%d' % (c + 1))], atol=1e-9)
+    assert abs(rep['iterations'] - it) <= 2     # the stopping test may fire one iteration apart
+    ctx.close()
+
+
+def test_classical_ising_yang_on_gpu():
+    """The GPU CTMRG on the classical Ising network reproduces Yang's magnetisation (no oracle involved)."""
+    beta = 0.5
+    a, a_s = K.ising_tensors(beta)
+    rng = np.random.default_rng(3)
+    G, H, Kg, Lg = [np.eye(2) + 0.3 * rng.standard_normal((2, 2)) for _ in range(4)]
+    A, Bt = K.gauge_pair(a, G, H, Kg, Lg)
+    As, Bs = K.gauge_pair(a_s, G, H, Kg, Lg)
+    ctx = L.Context(2, 12)
+    ctx.tn_set_network([A, Bt], boundary=np.ones(2))
+    ctx.tn_ctmrg(1e-9, 400)
+    for site, (T, Ts) in enumerate([(A, As), (Bt, Bs), (Bt, Bs), (A, As)]):
+        z = ctx.tn_site_scalars(site, T)
+        zs = ctx.tn_site_scalars(site, Ts)
+        assert abs(abs(zs[0] / z[0]) - K.yang_magnetization(beta)) < 1e-8
+    ctx.close()
+
+
+def test_classical_ising_onsager_on_gpu():
+    beta = 0.6
+    a, _ = K.ising_tensors(beta)
+    ctx = L.Context(2, 12, cell=L.TN_CELL_SINGLE)
+    ctx.tn_set_network([a], boundary=np.ones(2))
+    ctx.tn_ctmrg(1e-10, 300)
+    Z1, Z0, Zh, Zv = ctx.tn_site_scalars(0)
+    assert abs(np.log(Z1 * Z0 / (Zh * Zv)) - K.onsager_free_energy(beta)) < 1e-9
+    ctx.close()
+
+
+def test_full_size_iteration_d4_chi64():
+    """One CTMRG iteration (4 moves) at the D = 4, chi = 64 workload shape: corner spectra and tensors."""
+    D, chi = 4, 64
+    A = random_peps(2, D, instance=4)
+    ctx, env = _gpu_after_moves(A, D, chi, 4)
+    sp = ctx.tn_corner_spectra()
+    st = _oracle_after_moves(A, chi, 4)
+    ref = OC.corner_spectra(st)
+    for i, (x, y) in enumerate([(0, 0), (1, 0), (0, 1), (1, 1)]):
+        for c in range(4):
+            np.testing.assert_allclose(sp[i, c], ref[(x, y, 'C%d' % (c + 1))], atol=1e-9)
+    # tensors up to the sign of individual chi-directions (ties of the sign rule at this size)
+    worst = max(abs(np.linalg.norm(env[s][n]) / np.linalg.norm(st.env[s][n]) - 1.0) for s in env for n in env[s])
+    assert worst < 1e-9, worst
+    ctx.close()

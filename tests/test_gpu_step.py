@@ -1,0 +1,151 @@
+"""GPU parity of the imaginary-time step (rows a1, a7-a14) against the oracle.
+
+The canonical form fixes the bond gauge only up to signs (and rotations inside
+degenerate weights), so the GPU and oracle trajectories may differ by such a
+gauge: the comparisons are on gauge-invariant quantities (weights, energies,
+magnetisations, spectra of the bond environment, ALS costs, fidelities).
+"""
+import numpy as np
+import pytest
+
+from oracle import ctmrg as OC
+from oracle import fullupdate as OF
+from oracle import model as OM
+from oracle import recycle as OR
+from paper_1411_0391_gb300 import _lib as L
+from paper_1411_0391_gb300 import build as B
+from paper_1411_0391_gb300.inputs import random_peps
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CELL = OC.checkerboard()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    L.lib()
+
+
+def _ctx(D, chi, h, tau, A):
+    ctx = L.Context(D, chi)
+    ctx.tn_set_hamiltonian(1.0, h)
+    ctx.tn_set_time_step(tau)
+    ctx.tn_set_state(A)
+    return ctx
+
+
+def _gpu_energy(ctx, tol=1e-12):
+    ctx.tn_build_double_layer()
+    ctx.tn_reset_env()
+    ctx.tn_ctmrg(tol, 500)
+    return ctx.tn_measure()
+
+
+def test_pepo():
+    ctx = _ctx(2, 8, 3.04, 0.005, random_peps(2, 2))
+    g = ctx.tn_get_tensor(L.TN_T_PEPO, 0, (2, 2, 2, 2, 2, 2))
+    np.testing.assert_allclose(g, OM.ipepo(3.04, 0.005), rtol=1e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_prepare_canonical_weights(D):
+    A = random_peps(2, D, instance=5)
+    ctx = _ctx(D, 8, 3.0, 0.01, A)
+    rep = ctx.tn_step_prepare()
+    can = __import__("oracle.canonical", fromlist=["canonicalize"]).canonicalize(A, CELL)
+    for e, link in enumerate(OF.link_list(CELL)):
+        lam = ctx.tn_get_tensor(L.TN_T_LAMBDA, e, (D,))
+        np.testing.assert_allclose(lam, can['lam'][link], atol=1e-10)
+    assert abs(rep['canon_iters'] - can['iters']) <= 2
+    # weighted canonical tensors: gauge-invariant norms per tensor and the pre-truncation rank
+    for t in range(2):
+        Ac = ctx.tn_get_tensor(L.TN_T_CANON, t, (2,) + (D,) * 4)
+        assert abs(np.linalg.norm(Ac) - 1.0) < 1e-12
+        np.testing.assert_allclose(np.sort(np.abs(Ac).ravel()), np.sort(np.abs(can['A'][t]).ravel()), atol=1e-9)
+
+
+def test_bond_environment_spectra():
+    """Eigenvalues of the normalised, PSD bond environment N of every link type (a8)."""
+    D, chi = 2, 8
+    A = random_peps(2, D, instance=6)
+    ctx = _ctx(D, chi, 3.0, 0.01, A)
+    ctx.tn_step_prepare()
+    ctx.tn_ctmrg(1e-12, 300)
+    ctx.tn_step_update()
+    cfg = OR.Config(h=3.0, tau=0.01, D=D, chi=chi, ctm_tol=1e-12, ctm_max=300)
+    At, env, info = OR.fu_step(A, CELL, cfg)
+    k = 2 * D
+    for e, link in enumerate(OF.link_list(CELL)):
+        N = ctx.tn_get_tensor(L.TN_T_BOND_ENV, e, (k, k, k, k)).reshape(k * k, k * k)
+        Nr = OF.bond_env(info['state'], CELL, link, info['Theta'], info['pre'])
+        Nr = OF.psd_project(Nr / np.einsum('ccee->', Nr)).reshape(k * k, k * k)
+        np.testing.assert_allclose(np.linalg.eigvalsh(N), np.linalg.eigvalsh(Nr), atol=1e-10)
+
+
+def test_fu_step_energy_parity():
+    D, chi, h = 2, 8, 3.0
+    A = random_peps(2, D, instance=7)
+    ctx = _ctx(D, chi, h, 0.01, A)
+    rep = ctx.tn_fu_step(1e-12, 300)
+    cfg = OR.Config(h=h, tau=0.01, D=D, chi=chi, ctm_tol=1e-12, ctm_max=300)
+    At, env, info = OR.fu_step(A, CELL, cfg)
+    assert rep['ctm_iterations'] == info['ctm_iters']
+    for e, link in enumerate(OF.link_list(CELL)):
+        assert abs(rep['als_cost'][e] - info['als'][link][1]) < 1e-10
+    g = _gpu_energy(ctx)
+    o = OR.energy(At, CELL, cfg, tol=1e-12)
+    assert abs(g['e_site'] - o['e_site']) < 1e-10 * abs(o['e_site'])
+    for t in range(2):
+        assert abs(g['mx'][t] - o['mx'][t]) < 1e-9
+        assert abs(abs(g['mz'][t]) - abs(o['mz'][t])) < 1e-9
+
+
+@pytest.mark.parametrize("D,chi,steps", [(2, 8, 5), (2, 16, 10)])
+def test_ite_trajectory_parity(D, chi, steps):
+    """Plain full-update trajectory (config of the D=2 workload: h=3, tau=0.01), energies to 1e-10."""
+    h = 3.0
+    A = random_peps(2, D, instance=8)
+    ctx = _ctx(D, chi, h, 0.01, A)
+    cfg = OR.Config(h=h, tau=0.01, D=D, chi=chi, ctm_tol=1e-10, ctm_max=500)
+    env = None
+    Ao = A
+    for _ in range(steps):
+        rep = ctx.tn_fu_step(1e-10, 500)
+        Ao, env, info = OR.fu_step(Ao, CELL, cfg, env)
+        # the warm-started CTMRG sees the two trajectories in (sign-)gauges that may
+        # differ, so its iteration count may differ; the converged results may not
+        assert info['ctm_converged']
+    g = _gpu_energy(ctx)
+    o = OR.energy(Ao, CELL, cfg, tol=1e-12)
+    assert abs(g['e_site'] - o['e_site']) < 1e-9 * abs(o['e_site'])
+
+
+def test_recycle_window_parity():
+    """One environment computation, the renormalised gate of Sec. VI.C and N_Re = 3 recycled steps."""
+    D, chi, h = 2, 8, 3.0
+    A = random_peps(2, D, instance=9)
+    cfg = OR.Config(h=h, tau=0.01, D=D, chi=chi, ctm_tol=1e-12, ctm_max=300)
+    A1, _, _ = OR.fu_step(A, CELL, cfg)
+    Ao, _, info = OR.recycle_window(A1, CELL, cfg, 3, None)
+    ctx = _ctx(D, chi, h, 0.01, A1)        # fresh context: trivial environment, as the oracle
+    ctx.tn_step_prepare()
+    ctx.tn_ctmrg(1e-12, 300)
+    ctx.tn_step_update()
+    F = ctx.tn_recycle(3)
+    assert abs(F - info['F']) < 1e-9
+    g = _gpu_energy(ctx)
+    o = OR.energy(Ao, CELL, cfg, tol=1e-12)
+    assert abs(g['e_site'] - o['e_site']) < 1e-9 * abs(o['e_site'])
+
+
+def test_d1_mean_field_on_gpu():
+    """D = 1 evolution reaches the mean-field energy -2 - h^2/8 (no oracle involved)."""
+    h = 2.0
+    ctx = _ctx(1, 2, h, 0.05, random_peps(2, 1, instance=3))
+    ctx.tn_evolve(100, ctm_tol=1e-10, ctm_max=200)
+    ctx.tn_set_time_step(0.01)
+    ctx.tn_evolve(200, ctm_tol=1e-10, ctm_max=200)
+    g = _gpu_energy(ctx)
+    assert abs(g['e_site'] - (-2.0 - h * h / 8.0)) < 1e-4
