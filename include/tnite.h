@@ -45,6 +45,7 @@ extern "C" {
 #define TN_ENOCONV   -4   /* iteration cap reached (warning; results written) */
 #define TN_ENUMERIC  -5   /* NaN or Inf detected */
 #define TN_ESTATE    -6   /* call out of order (e.g. no state set) */
+#define TN_ESCRATCH  -7   /* problem larger than the fixed scratch of tn_truncated_svd_noalloc */
 
 /* ---- configuration ------------------------------------------------------ */
 #define TN_CELL_CHECKERBOARD 2
@@ -233,6 +234,27 @@ int tn_eigh_small(const double* dA, int n, int batch, double* dW, double* dV, vo
  * right basis.  Subspace iteration with Rayleigh-Ritz for m > 112. */
 int tn_truncated_svd(void* ctx, const double* dM, int m, int k, double* dU, double* dS,
                      double* dV, const double* warm);
+
+/* Allocation-free variant of tn_truncated_svd (the paper has no counterpart:
+ * this is a deployment convenience).  For callers that cannot allocate device
+ * memory when they need it -- device memory held by another allocator, code
+ * that must not take the device-wide synchronisation of cudaMalloc/cudaFree,
+ * or a plugin without a context workspace -- it takes only the caller's
+ * buffers (dM: m x m input, dU/dV: m x k, dS: k, warm: optional m x k start)
+ * and uses a fixed device array of 2^19 doubles (4 MiB) that the library
+ * reserves on every GPU that loads it, until the process exits.
+ *  - Limits: k <= 96 and k <= m; the (m, k) scratch need must fit the array
+ *    (e.g. m <= 1024 with k <= 64 fits; m <= 112 always fits), otherwise
+ *    TN_ESCRATCH and nothing is run.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - Every call on a device shares the array and leaves its contents behind:
+ *    calls that overlap on the GPU (other streams, other threads) race.
+ *    Nothing in the array is assumed to start at zero.
+ *  - stream: cudaStream_t (NULL = legacy default); the call synchronises it.
+ *    Returns TN_OK or TN_ENOCONV (subspace iteration cap reached). */
+int tn_truncated_svd_noalloc(const double* dM, int m, int k, double* dU, double* dS,
+                             double* dV, const double* warm, void* stream);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _PATH = os.path.join(_HERE, "libtnite.so")
 _LIB = None
 
-TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE = 0, -1, -2, -3, -4, -5, -6
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE, TN_ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
 TN_CELL_CHECKERBOARD, TN_CELL_SINGLE = 2, 1
 TN_F64 = 0
 (TN_T_STATE, TN_T_CANON, TN_T_LAMBDA, TN_T_THETA, TN_T_PRE_P, TN_T_PRE_Q, TN_T_DOUBLE,
@@ -83,6 +83,7 @@ _SIGS = {
     "tn_svd_small": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "tn_eigh_small": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "tn_truncated_svd": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tn_truncated_svd_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -162,6 +163,15 @@ def tn_truncated_svd(ctx, M, m, k, U, S, V, warm=None):
                                          c_void_p(S.data_ptr()), c_void_p(V.data_ptr()),
                                          c_void_p(0 if warm is None else warm.data_ptr())),
                   "tn_truncated_svd", allow_noconv=True)
+
+
+def tn_truncated_svd_noalloc(M, m, k, U, S, V, warm=None, stream=None):
+    """Allocation-free truncated SVD: only the caller's buffers, fixed 4 MiB library scratch."""
+    return _check(lib().tn_truncated_svd_noalloc(c_void_p(M.data_ptr()), m, k, c_void_p(U.data_ptr()),
+                                                 c_void_p(S.data_ptr()), c_void_p(V.data_ptr()),
+                                                 c_void_p(0 if warm is None else warm.data_ptr()),
+                                                 _stream_ptr(stream)),
+                  "tn_truncated_svd_noalloc", allow_noconv=True)
 
 
 # ---- context -----------------------------------------------------------------

@@ -160,6 +160,7 @@ const char* tn_strerror(int s)
         case TN_ENOCONV: return "iteration cap reached (results written)";
         case TN_ENUMERIC: return "NaN or Inf encountered";
         case TN_ESTATE: return "call out of order (state, time step or environment missing)";
+        case TN_ESCRATCH: return "problem larger than the fixed scratch of the allocation-free entry point";
         default: return "unknown status";
     }
 }
