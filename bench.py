@@ -30,6 +30,7 @@ METRIC = "CTMRG moves/s and ITE steps/s at D=4,χ=64; energy err vs FP64 oracle"
 WL = dict(D=4, chi=64, h=3.04, tau=0.005, cell="checkerboard")
 CTM_ITERS = 4
 MOVES_PER_STEP = 4 * CTM_ITERS
+N_RE = 5                            # recycled steps per environment computation (Sec. VI.C)
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (SIMT) at the 2070 MHz boost clock
 
 
@@ -245,6 +246,7 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)       # larger than the 129 MB L2
     t_prep = t_ctm = t_upd = 0.0
     launches = 0
+    svd_calls = svd_iters = 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -257,8 +259,10 @@ def run_gpu(args):
             ev[0].record(stream)
             ctx.tn_step_prepare()
             ev[1].record(stream)
-            ctx.tn_ctmrg(0.0, CTM_ITERS)
+            rep = ctx.tn_ctmrg(0.0, CTM_ITERS)
             ev[2].record(stream)
+            svd_calls += rep["svd_calls"]
+            svd_iters += rep["svd_iterations"]
             ctx.tn_step_update()
             ev[3].record(stream)
             torch.cuda.synchronize()
@@ -273,6 +277,23 @@ def run_gpu(args):
         total, t_ctm = float(t[0]), float(t[1])
     value = world * args.steps / total
     moves_per_s = world * args.steps * MOVES_PER_STEP / t_ctm
+
+    # recycled form (Sec. VI.C): one environment computation, then N_RE steps with the renormalised gate
+    t_rec = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.tn_step_prepare()
+        ctx.tn_ctmrg(0.0, CTM_ITERS)
+        ctx.tn_step_update()
+        F = ctx.tn_recycle(N_RE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_rec += e0.elapsed_time(e1) / 1e3
+    recycled = {"n_re": N_RE, "steps_per_s": world * args.steps * N_RE / t_rec,
+                "speedup_vs_plain": (args.steps * N_RE / t_rec) / (args.steps / total), "last_fidelity": F}
 
     # end to end through the public API with host buffers: H2D of the state, the step, D2H of the result
     import numpy as np
@@ -317,6 +338,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "moves_per_s": moves_per_s,
         "time_split_s": {"prepare": t_prep, "ctmrg": t_ctm, "update": t_upd},
+        "projector_svd": {"calls": svd_calls, "iterations_per_call": svd_iters / max(svd_calls, 1)},
+        "recycled": recycled,
         "config": dict(workload="ITE full-update step, 2D TFIM h=3.04 tau=0.005, checkerboard iPEPS D=4 chi=64, "
                                 "CTMRG budget %d iterations per step" % CTM_ITERS, **WL,
                        ctm_iterations_per_step=CTM_ITERS, parallelism="replicas" if world > 1 else "single",

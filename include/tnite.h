@@ -46,12 +46,15 @@ extern "C" {
 #define TN_ENUMERIC  -5   /* NaN or Inf detected */
 #define TN_ESTATE    -6   /* call out of order (e.g. no state set) */
 #define TN_ESCRATCH  -7   /* problem larger than the fixed scratch of tn_truncated_svd_noalloc */
+#define TN_ETIMEOUT  -8   /* a bounded device-side wait expired (tensor-core kernels); results invalid */
 
 /* ---- configuration ------------------------------------------------------ */
 #define TN_CELL_CHECKERBOARD 2
 #define TN_CELL_SINGLE       1
 
 #define TN_F64    0   /* every contraction in double */
+#define TN_TF32X3 1   /* split-precision tensor-core products, TF32 head + tail (tn_gemm_split) */
+#define TN_BF16X3 2   /* split-precision tensor-core products, BF16 head + tail (tn_gemm_split) */
 
 typedef struct tn_config {
     int D;          /* PEPS bond dimension, 1..8 */
@@ -94,6 +97,8 @@ typedef struct tn_ctm_report {
     int    converged;    /* 1 if delta < tol */
     double delta;        /* max over corners of ||s_new - s_old||_2 of the
                             sum-normalised corner singular values */
+    int    svd_calls;    /* projector SVDs computed in this call */
+    int    svd_iterations; /* subspace iterations summed over those SVDs */
 } tn_ctm_report;
 
 /* Build the double layers a = sum_s A^s (x) A^s of the current state (row a2),
@@ -217,6 +222,20 @@ int tn_gemm_f64(int transA, int transB, int m, int n, int k, double alpha,
                 const double* dA, int lda, long long strideA,
                 const double* dB, int ldb, long long strideB, double beta,
                 double* dC, int ldc, long long strideC, int batch, void* stream);
+/* Split-precision C = alpha op(A) op(B) + beta C on the tensor cores
+ * (precision TN_TF32X3 or TN_BF16X3; layout and op() as tn_gemm_f64, no
+ * batch).  Each FP64 operand is split into head and tail of the tensor-core
+ * type, x = hi + lo, and hi.hi + hi.lo + lo.hi is accumulated in FP32
+ * (about 2^-21 relative for TF32, 2^-16 for BF16); C is written in FP64.
+ * This is the contraction arithmetic of the precision form (the paper itself
+ * works in double throughout).  d_workspace (device, 256-byte aligned, caller
+ * owned) holds the split operands: at least tn_gemm_split_workspace_bytes().
+ * Returns TN_ENOMEM if it is smaller, TN_ETIMEOUT if a device-side wait of
+ * the kernel expired (C is then invalid); synchronises the stream. */
+size_t tn_gemm_split_workspace_bytes(int precision, int m, int n, int k);
+int tn_gemm_split(int precision, int transA, int transB, int m, int n, int k, double alpha,
+                  const double* dA, int lda, const double* dB, int ldb, double beta,
+                  double* dC, int ldc, void* d_workspace, size_t workspace_bytes, void* stream);
 /* Permute a rank <= 8 tensor: out[i_perm[0]]...[i_perm[r-1]] = in[i_0]..[i_{r-1}],
  * i.e. output axis j is input axis perm[j]; dims are the input dims. */
 int tn_permute_f64(const double* d_in, double* d_out, int rank, const int* dims,

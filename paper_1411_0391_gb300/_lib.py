@@ -17,7 +17,7 @@ _LIB = None
 
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE, TN_ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
 TN_CELL_CHECKERBOARD, TN_CELL_SINGLE = 2, 1
-TN_F64 = 0
+TN_F64, TN_TF32X3, TN_BF16X3 = 0, 1, 2
 (TN_T_STATE, TN_T_CANON, TN_T_LAMBDA, TN_T_THETA, TN_T_PRE_P, TN_T_PRE_Q, TN_T_DOUBLE,
  TN_T_BOND_ENV, TN_T_FU_P, TN_T_FU_Q, TN_T_GAUGE_W, TN_T_GATE_K, TN_T_PEPO) = range(13)
 
@@ -27,7 +27,8 @@ class tn_config(ctypes.Structure):
 
 
 class tn_ctm_report(ctypes.Structure):
-    _fields_ = [("iterations", c_int), ("converged", c_int), ("delta", c_double)]
+    _fields_ = [("iterations", c_int), ("converged", c_int), ("delta", c_double), ("svd_calls", c_int),
+                ("svd_iterations", c_int)]
 
 
 class tn_step_report(ctypes.Structure):
@@ -79,6 +80,9 @@ _SIGS = {
     "tn_get_tensor": (c_int, [c_void_p, c_int, c_int, _DP, c_size_t]),
     "tn_gemm_f64": (c_int, [c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_longlong,
                             c_void_p, c_int, c_longlong, c_double, c_void_p, c_int, c_longlong, c_int, c_void_p]),
+    "tn_gemm_split_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int]),
+    "tn_gemm_split": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
+                              c_double, c_void_p, c_int, c_void_p, c_size_t, c_void_p]),
     "tn_permute_f64": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_int), POINTER(c_int), c_void_p]),
     "tn_svd_small": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "tn_eigh_small": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
@@ -140,6 +144,18 @@ def tn_gemm_f64(transA, transB, m, n, k, alpha, A, lda, strideA, B, ldb, strideB
     _check(lib().tn_gemm_f64(int(transA), int(transB), m, n, k, alpha, c_void_p(A.data_ptr()), lda, strideA,
                              c_void_p(B.data_ptr()), ldb, strideB, beta, c_void_p(C.data_ptr()), ldc, strideC,
                              batch, _stream_ptr(stream)), "tn_gemm_f64")
+
+
+def tn_gemm_split_workspace_bytes(precision, m, n, k):
+    return int(lib().tn_gemm_split_workspace_bytes(precision, m, n, k))
+
+
+def tn_gemm_split(precision, transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, work, stream=None):
+    """work: a device tensor of at least tn_gemm_split_workspace_bytes bytes (256-byte aligned)."""
+    _check(lib().tn_gemm_split(precision, int(transA), int(transB), m, n, k, alpha, c_void_p(A.data_ptr()), lda,
+                               c_void_p(B.data_ptr()), ldb, beta, c_void_p(C.data_ptr()), ldc,
+                               c_void_p(work.data_ptr()), work.numel() * work.element_size(), _stream_ptr(stream)),
+           "tn_gemm_split")
 
 
 def tn_permute_f64(inp, out, dims, perm, stream=None):
@@ -242,7 +258,8 @@ class Context:
     def tn_ctmrg(self, tol, max_iter):
         rep = tn_ctm_report()
         s = _check(lib().tn_ctmrg(self.handle, tol, max_iter, byref(rep)), "tn_ctmrg", allow_noconv=True)
-        return dict(iterations=rep.iterations, converged=bool(rep.converged), delta=rep.delta, status=s)
+        return dict(iterations=rep.iterations, converged=bool(rep.converged), delta=rep.delta, status=s,
+                    svd_calls=rep.svd_calls, svd_iterations=rep.svd_iterations)
 
     def tn_ctmrg_moves(self, n):
         _check(lib().tn_ctmrg_moves(self.handle, n), "tn_ctmrg_moves")

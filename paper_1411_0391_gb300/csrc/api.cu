@@ -161,6 +161,7 @@ const char* tn_strerror(int s)
         case TN_ENUMERIC: return "NaN or Inf encountered";
         case TN_ESTATE: return "call out of order (state, time step or environment missing)";
         case TN_ESCRATCH: return "problem larger than the fixed scratch of the allocation-free entry point";
+        case TN_ETIMEOUT: return "a bounded device-side wait expired in a tensor-core kernel";
         default: return "unknown status";
     }
 }
@@ -445,6 +446,32 @@ int tn_gemm_f64(int transA, int transB, int m, int n, int k, double alpha,
     if (m < 0 || n < 0 || k < 0 || batch < 0 || (m * n > 0 && (!dA || !dB || !dC))) return TN_EINVAL;
     return gemm(reinterpret_cast<cudaStream_t>(stream), transA != 0, transB != 0, m, n, k, alpha,
                 dA, lda, strideA, dB, ldb, strideB, beta, dC, ldc, strideC, batch);
+}
+
+size_t tn_gemm_split_workspace_bytes(int precision, int m, int n, int k)
+{
+    if ((precision != TN_TF32X3 && precision != TN_BF16X3) || m < 1 || n < 1 || k < 1) return 0;
+    return gemm_tc_scratch_bytes(precision == TN_TF32X3 ? 0 : 1, m, n, k);
+}
+
+int tn_gemm_split(int precision, int transA, int transB, int m, int n, int k, double alpha,
+                  const double* dA, int lda, const double* dB, int ldb, double beta,
+                  double* dC, int ldc, void* d_workspace, size_t workspace_bytes, void* stream)
+{
+    if (precision != TN_TF32X3 && precision != TN_BF16X3) return TN_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || !dA || !dB || !dC || !d_workspace) return TN_EINVAL;
+    if (lda < (transA ? m : k) || ldb < (transB ? k : n) || ldc < n) return TN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_workspace) % 256) return TN_EINVAL;
+    const int kind = precision == TN_TF32X3 ? 0 : 1;
+    if (workspace_bytes < gemm_tc_scratch_bytes(kind, m, n, k)) return TN_ENOMEM;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Arena ar;
+    ar.base = static_cast<char*>(d_workspace);
+    ar.cap = workspace_bytes;
+    TN_TRY(gemm_tc(st, ar, kind, transA != 0, transB != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc));
+    int flag = 0;
+    TN_TRY(tc_status(st, &flag));
+    return flag ? TN_ETIMEOUT : TN_OK;
 }
 
 int tn_permute_f64(const double* d_in, double* d_out, int rank, const int* dims, const int* perm, void* stream)

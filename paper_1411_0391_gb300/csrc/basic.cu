@@ -100,6 +100,116 @@ int gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
 }
 
 // ---------------------------------------------------------------------------
+// split-K for products with few output tiles (Gram matrices, N x k panels):
+// each slice of k goes to its own set of blocks writing a partial product; a
+// second kernel sums the partials in slice order (deterministic).
+// ---------------------------------------------------------------------------
+__global__ void splitk_reduce_kernel(const double* __restrict__ P, int splits, int m, int n, double alpha,
+                                     double beta, double* __restrict__ C, int ldc)
+{
+    const long long mn = (long long)m * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mn;
+         e += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int s = 0; s < splits; ++s) acc += P[s * mn + e];
+        int r = (int)(e / n), c = (int)(e % n);
+        double* dst = C + (long long)r * ldc + c;
+        *dst = (beta == 0.0) ? alpha * acc : alpha * acc + beta * (*dst);
+    }
+}
+
+int gemm_splitk(cudaStream_t st, Arena& ar, bool ta, bool tb, int m, int n, int k, double alpha,
+                const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc)
+{
+    const int tiles = ((m + GT - 1) / GT) * ((n + GT - 1) / GT);
+    int splits = 1;
+    if (tiles < 152 && k >= 256) splits = std::min(std::max(1, 304 / tiles), std::max(1, k / 128));
+    if (splits <= 1) return gemm(st, ta, tb, m, n, k, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1);
+    int ks = (k + splits - 1) / splits;
+    ks = (ks + GK - 1) / GK * GK;
+    splits = (k + ks - 1) / ks;
+    size_t mk = ar.mark();
+    double* P = ar.take((size_t)splits * m * n);
+    if (!P) { ar.release(mk); return gemm(st, ta, tb, m, n, k, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1); }
+    const long long sA = ta ? (long long)ks * lda : ks;
+    const long long sB = tb ? ks : (long long)ks * ldb;
+    const int full = (k % ks == 0) ? splits : splits - 1;
+    if (full > 0) TN_TRY(gemm(st, ta, tb, m, n, ks, 1.0, A, lda, sA, B, ldb, sB, 0.0, P, n, (long long)m * n, full));
+    if (full < splits) {
+        const int kl = k - full * ks;
+        TN_TRY(gemm(st, ta, tb, m, n, kl, 1.0, A + full * sA, lda, 0, B + full * sB, ldb, 0, 0.0,
+                    P + (size_t)full * m * n, n, 0, 1));
+    }
+    long long mn = (long long)m * n;
+    int blocks = (int)std::min<long long>((mn + 255) / 256, 152 * 8);
+    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(P, splits, m, n, alpha, beta, C, ldc);
+    TN_LAUNCHED();
+    ar.release(mk);
+    return TN_OK;
+}
+
+// Column norms of a row-major rows x cols matrix; columns scaled to unit norm
+// (columns of norm zero stay zero).  One block per column.
+__global__ void normalize_cols_kernel(double* Y, int rows, int cols)
+{
+    const int j = blockIdx.x;
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) { double v = Y[(long long)i * cols + j]; acc = fma(v, v, acc); }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        red[0] = t;
+    }
+    __syncthreads();
+    const double nrm = sqrt(red[0]);
+    if (nrm == 0.0) return;
+    const double inv = 1.0 / nrm;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) Y[(long long)i * cols + j] *= inv;
+}
+
+int normalize_cols(cudaStream_t st, double* Y, int rows, int cols)
+{
+    if (cols <= 0) return TN_OK;
+    normalize_cols_kernel<<<cols, 256, 0, st>>>(Y, rows, cols);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// rn[j] = || R[:, j] - U[:, j] s[j] ||_2 for j < k (row-major, leading dims ldr, ldu)
+__global__ void residual_norms_kernel(const double* __restrict__ R, int ldr, const double* __restrict__ U, int ldu,
+                                      const double* __restrict__ s, int rows, double* __restrict__ rn)
+{
+    const int j = blockIdx.x;
+    __shared__ double red[32];
+    const double sj = s[j];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        double d = R[(long long)i * ldr + j] - U[(long long)i * ldu + j] * sj;
+        acc = fma(d, d, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        rn[j] = sqrt(t);
+    }
+}
+
+int residual_norms(cudaStream_t st, const double* R, int ldr, const double* U, int ldu, const double* s,
+                   int rows, int k, double* rn)
+{
+    residual_norms_kernel<<<k, 256, 0, st>>>(R, ldr, U, ldu, s, rows, rn);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// ---------------------------------------------------------------------------
 // permutation: output axis j is input axis perm[j]
 // ---------------------------------------------------------------------------
 struct PermArgs {

@@ -162,6 +162,8 @@ static int cut_projectors(Ctx& c, Frame& f, int x, int y, double* Pup, double* P
     TsvdStats stats;
     int s = truncated_svd(c.st, c.ar, rho, N, chi, U, S, Vw, c.warm_ok[f.rot][xx][yy] ? Vw : nullptr, &stats);
     if (s != TN_OK && s != TN_ENOCONV) return s;
+    c.svd_calls += 1;
+    c.svd_iterations += stats.iterations;
     c.warm_ok[f.rot][xx][yy] = true;
     // P_up = R_d^T U S^{-1/2}, P_lo = R_u V S^{-1/2}
     TN_TRY(gemm(c.st, true, false, N, chi, N, 1.0, Rd, N, 0, U, chi, 0, 0.0, Pup, chi, 0, 1));
@@ -276,6 +278,7 @@ int corner_spectra(Ctx& c, std::vector<double>& out)
 int ctmrg_iterations(Ctx& c, double tol, int max_iter, tn_ctm_report* rep)
 {
     std::vector<double> cur;
+    const long long calls0 = c.svd_calls, iters0 = c.svd_iterations;
     if (c.prev_spectra.empty()) TN_TRY(corner_spectra(c, c.prev_spectra));
     double delta = INFINITY;
     int it = 0;
@@ -294,11 +297,17 @@ int ctmrg_iterations(Ctx& c, double tol, int max_iter, tn_ctm_report* rep)
             delta = std::max(delta, std::sqrt(acc));
         }
         c.prev_spectra = cur;
-        if (!std::isfinite(delta)) { if (rep) { rep->iterations = it; rep->converged = 0; rep->delta = delta; } return TN_ENUMERIC; }
+        if (!std::isfinite(delta)) {
+            if (rep) { rep->iterations = it; rep->converged = 0; rep->delta = delta; rep->svd_calls = 0; rep->svd_iterations = 0; }
+            return TN_ENUMERIC;
+        }
         if (delta < tol) { conv = true; break; }
     }
     if (it > max_iter) it = max_iter;
-    if (rep) { rep->iterations = it; rep->converged = conv ? 1 : 0; rep->delta = delta; }
+    if (rep) {
+        rep->iterations = it; rep->converged = conv ? 1 : 0; rep->delta = delta;
+        rep->svd_calls = (int)(c.svd_calls - calls0); rep->svd_iterations = (int)(c.svd_iterations - iters0);
+    }
     return conv ? TN_OK : TN_ENOCONV;
 }
 

@@ -68,6 +68,7 @@ struct Ctx {
     double* hbuf = nullptr;
 
     long long ctm_moves = 0;
+    long long svd_calls = 0, svd_iterations = 0;
     std::vector<double> prev_spectra;
 
     int N() const { return chi * leg; }

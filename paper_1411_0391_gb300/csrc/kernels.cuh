@@ -10,6 +10,11 @@ struct TsvdStats { int iterations = 0; };
 int gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
          const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
          double beta, double* C, int ldc, long long sC, int batch);
+int gemm_splitk(cudaStream_t st, Arena& ar, bool ta, bool tb, int m, int n, int k, double alpha,
+                const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
+int normalize_cols(cudaStream_t st, double* Y, int rows, int cols);
+int residual_norms(cudaStream_t st, const double* R, int ldr, const double* U, int ldu, const double* s,
+                   int rows, int k, double* rn);
 int permute(cudaStream_t st, const double* in, double* out, int rank, const int* dims, const int* perm);
 int scale_rows(cudaStream_t st, double* C, int m, int n, int ldc, double s);
 int normalize_maxabs(cudaStream_t st, double* x, long long n, int batch, long long stride);
@@ -23,8 +28,18 @@ int eigh_small(cudaStream_t st, const double* A, int n, int batch, double* W, do
 int chol_inv(cudaStream_t st, const double* G, int n, double c_shift, double* X);
 int sign_fix_cols(cudaStream_t st, double* U, double* V, int rows, int vrows, int cols);
 int orth(cudaStream_t st, Arena& ar, double* Y, int rows, int cols);
+int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, bool shifted);
+int tsvd_columns(int m, int k);
 int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
                   double* U, double* S, double* V, const double* warm, TsvdStats* stats);
+
+// tc_gemm.cu: split-precision products on the tensor cores (kind 0 = TF32 x3,
+// 1 = BF16 x3); tc_status reads and clears the device-side wait flag.
+int tc_tile_n(int m, int n);
+size_t gemm_tc_scratch_bytes(int kind, int m, int n, int k);
+int gemm_tc(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,
+            const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
+int tc_status(cudaStream_t st, int* status);
 
 // contract.cu: C = alpha * A.B (+ beta C when no output permutation is needed),
 // einsum-style labels "ab,bcm->acm" (no traces, no batch labels).

@@ -174,21 +174,37 @@ int sign_fix_cols(cudaStream_t st, double* U, double* V, int rows, int vrows, in
 }
 
 // ---------------------------------------------------------------------------
-// orthonormalisation (shifted CholeskyQR3) of Y (rows x cols, row-major)
+// orthonormalisation of Y (rows x cols, row-major)
 // ---------------------------------------------------------------------------
+// orth: shifted CholeskyQR3 (Fukaya et al.): a shifted pass, then two plain ones.
 int orth(cudaStream_t st, Arena& ar, double* Y, int rows, int cols)
+{
+    size_t mk = ar.mark();
+    double* T = ar.take((size_t)rows * cols);
+    if (!T) { ar.release(mk); return TN_ENOMEM; }
+    int s = orth2(st, ar, Y, T, rows, cols, true);
+    ar.release(mk);
+    return s;
+}
+
+// orth2: columns scaled to unit norm, then Cholesky-QR passes (three with the
+// first shifted, or two plain ones for a basis that is already close to
+// orthogonal up to column scales, as the Ritz panels of the subspace iteration).
+// tmp: rows x cols of caller scratch.
+int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, bool shifted)
 {
     size_t mk = ar.mark();
     double* G = ar.take((size_t)cols * cols);
     double* X = ar.take((size_t)cols * cols);
-    double* T = ar.take((size_t)rows * cols);
-    if (!G || !X || !T) { ar.release(mk); return TN_ENOMEM; }
+    if (!G || !X) { ar.release(mk); return TN_ENOMEM; }
+    TN_TRY(normalize_cols(st, Y, rows, cols));
     const double c_first = 11.0 * ((double)rows * cols + (double)cols * (cols + 1));
-    for (int pass = 0; pass < 3; ++pass) {
-        TN_TRY(gemm(st, true, false, cols, cols, rows, 1.0, Y, cols, 0, Y, cols, 0, 0.0, G, cols, 0, 1));
-        TN_TRY(chol_inv(st, G, cols, pass == 0 ? c_first : 0.0, X));
-        TN_TRY(gemm(st, false, false, rows, cols, cols, 1.0, Y, cols, 0, X, cols, 0, 0.0, T, cols, 0, 1));
-        TN_CUDA(cudaMemcpyAsync(Y, T, sizeof(double) * rows * cols, cudaMemcpyDeviceToDevice, st));
+    const int passes = shifted ? 3 : 2;
+    for (int pass = 0; pass < passes; ++pass) {
+        TN_TRY(gemm_splitk(st, ar, true, false, cols, cols, rows, 1.0, Y, cols, Y, cols, 0.0, G, cols));
+        TN_TRY(chol_inv(st, G, cols, (shifted && pass == 0) ? c_first : 0.0, X));
+        TN_TRY(gemm(st, false, false, rows, cols, cols, 1.0, Y, cols, 0, X, cols, 0, 0.0, tmp, cols, 0, 1));
+        TN_CUDA(cudaMemcpyAsync(Y, tmp, sizeof(double) * rows * cols, cudaMemcpyDeviceToDevice, st));
     }
     ar.release(mk);
     return TN_OK;
@@ -197,6 +213,15 @@ int orth(cudaStream_t st, Arena& ar, double* Y, int rows, int cols)
 // ---------------------------------------------------------------------------
 // truncated SVD
 // ---------------------------------------------------------------------------
+// Top-k triplets of the m x m matrix M (row-major).  m <= SMALL_MAX: one-sided
+// Jacobi on M.  Otherwise subspace iteration on kk = k + max(8, k/4) columns:
+//   Y = orth(M Om), Z = orth(M^T Y), T = M Z, B = Y^T T = Ub Sb Vb^T,
+//   Ritz vectors U_r = Y Ub, V_r = Z Vb; the next basis is Om = V_r, so B is
+//   nearly diagonal from the second iteration on.  Stop when every kept Ritz
+//   pair has || M v_i - s_i u_i || = || T vb_i - s_i u_i || <= 1e-13 s_1 (an
+//   absolute test: directions at the noise floor pass it too), cap 16.
+// All products run as (split-K) GEMMs over the GPU; the kk x kk Cholesky and
+// SVD run in one block each.  No heap allocation: host data lives on the stack.
 int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
                   double* U, double* S, double* V, const double* warm, TsvdStats* stats)
 {
@@ -215,46 +240,56 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
         ar.release(mk);
         return TN_OK;
     }
-    int kk = std::min(m, std::min(SMALL_MAX, k + std::max(8, k / 4)));
+    const int kk = tsvd_columns(m, k);
     double* Om = ar.take((size_t)m * kk);
     double* Y = ar.take((size_t)m * kk);
     double* Z = ar.take((size_t)m * kk);
     double* T = ar.take((size_t)m * kk);
+    double* TV = ar.take((size_t)m * k);
+    double* Ur = ar.take((size_t)m * k);
     double* B = ar.take((size_t)kk * kk);
     double* Ub = ar.take((size_t)kk * kk);
-    double* Sb = ar.take(kk);
     double* Vb = ar.take((size_t)kk * kk);
-    if (!Om || !Y || !Z || !T || !B || !Ub || !Sb || !Vb) { ar.release(mk); return TN_ENOMEM; }
+    double* Sb = ar.take(kk);
+    double* rn = ar.take(kk);
+    if (!Om || !Y || !Z || !T || !TV || !Ur || !B || !Ub || !Vb || !Sb || !rn) { ar.release(mk); return TN_ENOMEM; }
     TN_TRY(hash_fill(st, Om, (long long)m * kk, 0x5eed0000ull + (unsigned long long)m * 131 + k));
     if (warm)
         TN_CUDA(cudaMemcpy2DAsync(Om, kk * sizeof(double), warm, k * sizeof(double), k * sizeof(double), m, cudaMemcpyDeviceToDevice, st));
-    std::vector<double> prev(kk, -1.0), cur(kk);
+    double hs[SMALL_MAX], hr[SMALL_MAX];
     const int max_it = 16;
     int it = 0;
-    for (; it < max_it; ++it) {
-        TN_TRY(gemm(st, false, false, m, kk, m, 1.0, M, m, 0, Om, kk, 0, 0.0, Y, kk, 0, 1));
-        TN_TRY(orth(st, ar, Y, m, kk));
-        TN_TRY(gemm(st, true, false, m, kk, m, 1.0, M, m, 0, Y, kk, 0, 0.0, Z, kk, 0, 1));
-        TN_TRY(orth(st, ar, Z, m, kk));
-        TN_TRY(gemm(st, false, false, m, kk, m, 1.0, M, m, 0, Z, kk, 0, 0.0, T, kk, 0, 1));
-        TN_TRY(gemm(st, true, false, kk, kk, m, 1.0, Y, kk, 0, T, kk, 0, 0.0, B, kk, 0, 1));
+    bool conv = false;
+    for (it = 1; it <= max_it; ++it) {
+        const bool first = (it == 1);
+        TN_TRY(gemm_splitk(st, ar, false, false, m, kk, m, 1.0, M, m, Om, kk, 0.0, Y, kk));
+        TN_TRY(orth2(st, ar, Y, T, m, kk, first));
+        TN_TRY(gemm_splitk(st, ar, true, false, m, kk, m, 1.0, M, m, Y, kk, 0.0, Z, kk));
+        TN_TRY(orth2(st, ar, Z, T, m, kk, first));
+        TN_TRY(gemm_splitk(st, ar, false, false, m, kk, m, 1.0, M, m, Z, kk, 0.0, T, kk));
+        TN_TRY(gemm_splitk(st, ar, true, false, kk, kk, m, 1.0, Y, kk, T, kk, 0.0, B, kk));
         TN_TRY(svd_small(st, B, kk, kk, 1, Ub, Sb, Vb));
-        TN_CUDA(cudaMemcpyAsync(cur.data(), Sb, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TN_TRY(gemm(st, false, false, m, k, kk, 1.0, Y, kk, 0, Ub, kk, 0, 0.0, Ur, k, 0, 1));     // U_r
+        TN_TRY(gemm(st, false, false, m, k, kk, 1.0, T, kk, 0, Vb, kk, 0, 0.0, TV, k, 0, 1));     // M V_r
+        TN_TRY(residual_norms(st, TV, k, Ur, k, Sb, m, k, rn));
+        TN_TRY(gemm(st, false, false, m, kk, kk, 1.0, Z, kk, 0, Vb, kk, 0, 0.0, Om, kk, 0, 1));   // V_r -> next basis
+        TN_CUDA(cudaMemcpyAsync(hs, Sb, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TN_CUDA(cudaMemcpyAsync(hr, rn, k * sizeof(double), cudaMemcpyDeviceToHost, st));
         TN_CUDA(cudaStreamSynchronize(st));
-        double dmax = 0.0;
-        for (int i = 0; i < k; ++i) dmax = std::max(dmax, std::fabs(cur[i] - prev[i]));
-        prev = cur;
-        std::swap(Om, Z);
-        if (it >= 1 && dmax <= 1e-14 * std::max(cur[0], 1e-300)) { ++it; break; }
+        double worst = 0.0;
+        for (int i = 0; i < k; ++i) worst = std::max(worst, hr[i]);
+        if (worst <= 1e-13 * std::max(hs[0], 1e-300)) { conv = true; break; }
     }
-    // after the swap, Om holds the last Z
-    TN_TRY(gemm(st, false, false, m, k, kk, 1.0, Y, kk, 0, Ub, kk, 0, 0.0, U, k, 0, 1));
-    TN_TRY(gemm(st, false, false, m, k, kk, 1.0, Om, kk, 0, Vb, kk, 0, 0.0, V, k, 0, 1));
+    if (it > max_it) it = max_it;
+    TN_CUDA(cudaMemcpyAsync(U, Ur, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, st));
+    TN_CUDA(cudaMemcpy2DAsync(V, k * sizeof(double), Om, kk * sizeof(double), k * sizeof(double), m, cudaMemcpyDeviceToDevice, st));
     TN_CUDA(cudaMemcpyAsync(S, Sb, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TN_TRY(sign_fix_cols(st, U, V, m, m, k));
     if (stats) stats->iterations = it;
     ar.release(mk);
-    return it > max_it ? TN_ENOCONV : TN_OK;
+    return conv ? TN_OK : TN_ENOCONV;
 }
+
+int tsvd_columns(int m, int k) { return std::min(m, std::min(SMALL_MAX, k + std::max(8, k / 4))); }
 
 }  // namespace tn

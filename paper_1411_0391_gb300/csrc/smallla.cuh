@@ -116,7 +116,9 @@ static __device__ int blk_eigh_jacobi(double* A, int n, double* V, double* cs, i
         }
         off = block_sum(off, red);
         dia = block_sum(dia, red);
-        if (off <= 1e-30 * (dia + off) || off == 0.0) break;
+        // relative off-diagonal norm at the rounding floor of n-term sums
+        const double eps_n = fmax(1e-15, (double)n * 1e-16);
+        if (off <= eps_n * eps_n * (dia + off) || off == 0.0) break;
         for (int r = 0; r < M - 1; ++r) {
             for (int k = threadIdx.x; k < H; k += blockDim.x) {
                 int p, q;

@@ -1,0 +1,473 @@
+// Split-precision GEMM on the fifth-generation tensor cores (tcgen05).
+//
+// C = alpha op(A) op(B) + beta C with FP64 inputs and output.  Each operand is
+// split into a TF32 head and a TF32 tail, x = hi + lo with hi = tf32(x) and
+// lo = tf32(x - hi) (|x - hi - lo| <= 2^-22 |x|), and the product is taken as
+//     hi_A hi_B  +  (hi_A lo_B + lo_A hi_B)
+// on the tensor cores (the dropped lo_A lo_B term is 2^-22 relative).  The
+// BF16 variant splits into bfloat16 head and tail the same way (2^-16).
+//
+// Accumulation.  A tensor-core FP32 accumulator that runs over the whole K
+// loses about one unit in the last place per accumulation step, which over
+// K = 1024 is ~1e-5 relative.  Here every 128-byte K block (32 TF32 or 64
+// BF16 terms) starts fresh accumulators in tensor memory, one for the head
+// product and one for the two correction products, and the epilogue warps
+// add each finished block into double-float (hi + lo FP32 pair, TwoSum)
+// registers while the tensor cores work on the next block.  Tensor memory
+// holds two such accumulator pairs (double buffering).
+//
+// Roles in one CTA (one 128 x 64 tile of C, 160 threads):
+//   * warp 4, lane 0: TMA loads of 128-byte K slices (128-byte swizzle) into a
+//     4-deep ring of shared-memory stages, each guarded by an mbarrier that
+//     counts the landed bytes; tcgen05.mma of the three products per 32-byte
+//     K step; tcgen05.commit to release the stage and to publish the
+//     accumulator buffer;
+//   * warps 0-3: wait for a published buffer, read it with tcgen05.ld (warp w
+//     owns TMEM lanes 32w..32w+31 = rows of the tile), accumulate, hand the
+//     buffer back through an mbarrier; finally write alpha acc + beta C.
+// Every mbarrier wait is bounded (about one second of device time); on expiry
+// the kernel records an error in g_tc_status, drains its own outstanding TMA
+// loads (again bounded), frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <algorithm>
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace tn {
+
+static __device__ int g_tc_status;     // 0 = fine, else a wait expired in a tensor-core kernel
+
+namespace {
+
+constexpr int BM = 128;                 // rows of a C tile = UMMA M = TMEM lanes
+constexpr uint32_t ROWB = 128;          // bytes of K per operand row and stage (one swizzle row)
+constexpr unsigned long long WAIT_NS = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(a) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false after WAIT_NS.
+__device__ bool mbar_wait(uint32_t a, uint32_t parity)
+{
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(a, parity))
+        if (gtimer() - t0 > WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int KIND>
+__device__ __forceinline__ void tc_mma(uint32_t d, unsigned long long a, unsigned long long b, uint32_t idesc,
+                                       uint32_t acc)
+{
+    if constexpr (KIND == 0) {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+    } else {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+    }
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(bar) : "memory");
+}
+
+// 16 consecutive 32-bit columns of the warp's 32 TMEM lanes (one row per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzled layout written by TMA: rows of 128 bytes, 8-row groups 1024 bytes
+// apart (stride byte offset), leading byte offset unused for this layout,
+// descriptor version 1, swizzle mode 2 (128 bytes).  The tile base is 1024-byte
+// aligned; a K step inside the swizzle row advances the start address.
+__device__ __forceinline__ unsigned long long smem_desc(uint32_t saddr)
+{
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)1 << 16;                    // leading byte offset (16 B, ignored)
+    d |= (unsigned long long)(1024u >> 4) << 32;         // stride byte offset
+    d |= (unsigned long long)1 << 46;                    // descriptor version
+    d |= (unsigned long long)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A and B of the kind's type, both
+// K-major, N = bn, M = 128.
+template <int KIND>
+__host__ __device__ constexpr uint32_t instr_desc(int bn)
+{
+    return (1u << 4)                                          // D format: F32
+         | ((KIND == 0 ? 2u : 1u) << 7)                       // A format: TF32 / BF16
+         | ((KIND == 0 ? 2u : 1u) << 10)                      // B format
+         | ((uint32_t)(bn >> 3) << 17)                        // N >> 3
+         | ((uint32_t)(BM >> 4) << 24);                       // M >> 4
+}
+
+constexpr int BN = 64;                  // columns of a C tile = UMMA N
+constexpr int STAGES = 4;
+constexpr uint32_t A_BYTES = BM * ROWB, B_BYTES = BN * ROWB;
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // hi and lo of both operands
+constexpr uint32_t TMEM_COLS = 4 * BN;                          // 2 buffers x (head, correction)
+constexpr int THREADS = 160;                                    // 4 epilogue warps + 1 issuing warp
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+
+// s + x as an unevaluated FP32 pair (Knuth's TwoSum), lo collecting the rounding error.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += err;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               int Mp, int Np, int nkb, int M, int N, double alpha, double beta, double* __restrict__ C,
+               int ldc)
+{
+    constexpr int KEL = KIND == 0 ? 32 : 64;            // K elements per 128-byte row
+    constexpr uint32_t IDESC = instr_desc<KIND>(BN);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // barriers: full[STAGES], empty[STAGES], tfull[2], tfree[2]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES;
+    const uint32_t tfull0 = empty0 + 8 * STAGES, tfree0 = tfull0 + 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(full0 + 8 * s, 1); mbar_init(empty0 + 8 * s, 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(tfull0 + 8 * b, 1); mbar_init(tfree0 + 8 * b, 128); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            auto load = [&](int kb) {
+                const int s = kb % STAGES;
+                const uint32_t st = sbase + s * STAGE_BYTES, bar = full0 + 8 * s;
+                mbar_expect_tx(bar, STAGE_BYTES);
+                tma_load_2d(st, &mapA, kb * KEL, m0, bar);
+                tma_load_2d(st + A_BYTES, &mapA, kb * KEL, Mp + m0, bar);
+                tma_load_2d(st + 2 * A_BYTES, &mapB, kb * KEL, n0, bar);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapB, kb * KEL, Np + n0, bar);
+            };
+            bool ok = true;
+            int issued = 0, kb = 0;
+            for (; issued < STAGES && issued < nkb; ++issued) load(issued);
+            for (; kb < nkb; ++kb) {
+                const int s = kb % STAGES, b = kb & 1;
+                if (kb >= 2 && !mbar_wait(tfree0 + 8 * b, ((kb >> 1) - 1) & 1)) { ok = false; break; }
+                if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t st = sbase + s * STAGE_BYTES;
+                const unsigned long long ah = smem_desc(st), al = smem_desc(st + A_BYTES);
+                const unsigned long long bh = smem_desc(st + 2 * A_BYTES), bl = smem_desc(st + 2 * A_BYTES + B_BYTES);
+                const uint32_t t_head = tmem + (uint32_t)(b * 2 * BN), t_corr = t_head + BN;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {                 // 32 bytes of K per product
+                    const unsigned long long o = (unsigned long long)(ks * 2);   // 32 B >> 4
+                    tc_mma<KIND>(t_head, ah + o, bh + o, IDESC, ks != 0);
+                    tc_mma<KIND>(t_corr, ah + o, bl + o, IDESC, ks != 0);
+                    tc_mma<KIND>(t_corr, al + o, bh + o, IDESC, 1);
+                }
+                tc_commit(empty0 + 8 * s);
+                tc_commit(tfull0 + 8 * b);
+                if (kb >= 1 && issued < nkb) {                   // refill the stage k-block kb-1 used
+                    const int sp = (kb - 1) % STAGES;
+                    if (!mbar_wait(empty0 + 8 * sp, ((kb - 1) / STAGES) & 1)) { ok = false; ++kb; break; }
+                    load(issued);
+                    ++issued;
+                }
+            }
+            if (!ok) {
+                for (int j = kb; j < issued; ++j) mbar_wait(full0 + 8 * (j % STAGES), (j / STAGES) & 1);
+                atomicExch(&g_tc_status, 1);
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue warps: row of the tile = TMEM lane
+        float acc_hi[BN], acc_lo[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) { acc_hi[j] = 0.0f; acc_lo[j] = 0.0f; }
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int b = kb & 1;
+            if (!mbar_wait(tfull0 + 8 * b, (kb >> 1) & 1)) ok = false;
+            ok = __all_sync(0xffffffffu, ok);        // warp-uniform: tcgen05.ld is warp-collective
+            tc_fence_after();
+            const uint32_t t_head = tmem + lane_off + (uint32_t)(b * 2 * BN), t_corr = t_head + BN;
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t h[16], c[16];
+                tmem_ld16(t_head + (uint32_t)c0, h);
+                tmem_ld16(t_corr + (uint32_t)c0, c);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    two_sum_acc(acc_hi[c0 + j], acc_lo[c0 + j], __uint_as_float(h[j]));
+                    acc_lo[c0 + j] += __uint_as_float(c[j]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tfree0 + 8 * b);
+            if (!ok) break;
+        }
+        if (!ok) atomicExch(&g_tc_status, 2);
+        const int row = m0 + warp * 32 + lane;
+        if (row < M) {
+            double* crow = C + (size_t)row * ldc;
+#pragma unroll
+            for (int j = 0; j < BN; ++j) {
+                const int col = n0 + j;
+                if (col < N) {
+                    double v = alpha * ((double)acc_hi[j] + (double)acc_lo[j]);
+                    if (beta != 0.0) v += beta * crow[col];
+                    crow[col] = v;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// operand split: FP64 -> head/tail of the tensor-core type, K-major, padded
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_rn(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7f800000u) != 0x7f800000u) u += 0xfffu + ((u >> 13) & 1u);   // round to nearest even
+    return __uint_as_float(u & 0xffffe000u);
+}
+
+__device__ __forceinline__ void split_store(float* out, size_t hi_at, size_t lo_at, double x)
+{
+    const float h = tf32_rn((float)x);
+    out[hi_at] = h;
+    out[lo_at] = tf32_rn((float)(x - (double)h));
+}
+
+__device__ __forceinline__ void split_store(__nv_bfloat16* out, size_t hi_at, size_t lo_at, double x)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+    out[hi_at] = h;
+    out[lo_at] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+}
+
+// Logical operand X (R x K): element (r, k) at X[r*ld + k] when kcontig, else
+// at X[k*ld + r].  Output rows r < Rp: hi at out[r*Kp + k], lo at
+// out[(Rp + r)*Kp + k]; zero outside R x K.  32 x 32 tiles, 32 x 8 threads.
+template <typename T>
+__global__ void split_kernel(const double* __restrict__ X, int ld, int kcontig, int R, int K, int Rp, int Kp,
+                             T* __restrict__ out)
+{
+    __shared__ double tile[32][33];
+    const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (kcontig) {
+        for (int i = ty; i < 32; i += 8) {
+            const int r = r0 + i, k = k0 + tx;
+            tile[i][tx] = (r < R && k < K) ? X[(size_t)r * ld + k] : 0.0;
+        }
+    } else {
+        for (int i = ty; i < 32; i += 8) {
+            const int k = k0 + i, r = r0 + tx;
+            tile[tx][i] = (r < R && k < K) ? X[(size_t)k * ld + r] : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int r = r0 + i, k = k0 + tx;
+        split_store(out, (size_t)r * Kp + k, (size_t)(Rp + r) * Kp + k, tile[i][tx]);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int encoder()
+{
+    if (g_encode) return TN_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    TN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return TN_ECUDA;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return TN_OK;
+}
+
+// 2D map over a (2*rows_p) x Kp operand buffer, box = 128 bytes of K x box_rows.
+int make_map(CUtensorMap* map, int kind, void* base, int rows2, int Kp, int box_rows)
+{
+    const int esz = kind == 0 ? 4 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows2};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * esz};
+    cuuint32_t box[2] = {ROWB / (cuuint32_t)esz, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? TN_OK : TN_ECUDA;
+}
+
+template <int KIND>
+int launch_tc(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int Mp, int Np, int nkb, int m, int n,
+              double alpha, double beta, double* C, int ldc)
+{
+    static bool attr = false;
+    if (!attr) {
+        TN_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_BYTES));
+        attr = true;
+    }
+    dim3 grid(Np / BN, Mp / BM);
+    tc_gemm_kernel<KIND><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, Mp, Np, nkb, m, n, alpha, beta, C, ldc);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+inline int round_up(int x, int q) { return (x + q - 1) / q * q; }
+
+}  // namespace
+
+int tc_tile_n(int, int) { return BN; }
+
+size_t gemm_tc_scratch_bytes(int kind, int m, int n, int k)
+{
+    const int bn = tc_tile_n(m, n);
+    const int kq = kind == 0 ? 32 : 64;
+    const size_t esz = kind == 0 ? 4 : 2;
+    const size_t Mp = round_up(m, BM), Np = round_up(n, bn), Kp = round_up(k, kq);
+    return tn_align256(2 * Mp * Kp * esz) + tn_align256(2 * Np * Kp * esz);
+}
+
+int gemm_tc(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,
+            const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc)
+{
+    if (m < 1 || n < 1 || k < 1 || (kind != 0 && kind != 1)) return TN_EINVAL;
+    TN_TRY(encoder());
+    const int bn = tc_tile_n(m, n);
+    const int kq = kind == 0 ? 32 : 64;
+    const size_t esz = kind == 0 ? 4 : 2;
+    const int Mp = round_up(m, BM), Np = round_up(n, bn), Kp = round_up(k, kq);
+    const size_t mark = ar.mark();
+    void* As = ar.take((2 * (size_t)Mp * Kp * esz + 7) / 8);
+    void* Bs = ar.take((2 * (size_t)Np * Kp * esz + 7) / 8);
+    if (!As || !Bs) { ar.release(mark); return TN_ENOMEM; }
+    // A: rows m, K-contiguous unless transposed; B: rows n, K-contiguous only when transposed
+    dim3 blk(32, 8);
+    if (kind == 0) {
+        split_kernel<float><<<dim3(Kp / 32, Mp / 32), blk, 0, st>>>(A, lda, ta ? 0 : 1, m, k, Mp, Kp, (float*)As);
+        TN_LAUNCHED();
+        split_kernel<float><<<dim3(Kp / 32, Np / 32), blk, 0, st>>>(B, ldb, tb ? 1 : 0, n, k, Np, Kp, (float*)Bs);
+        TN_LAUNCHED();
+    } else {
+        split_kernel<__nv_bfloat16><<<dim3(Kp / 32, Mp / 32), blk, 0, st>>>(A, lda, ta ? 0 : 1, m, k, Mp, Kp,
+                                                                             (__nv_bfloat16*)As);
+        TN_LAUNCHED();
+        split_kernel<__nv_bfloat16><<<dim3(Kp / 32, Np / 32), blk, 0, st>>>(B, ldb, tb ? 1 : 0, n, k, Np, Kp,
+                                                                             (__nv_bfloat16*)Bs);
+        TN_LAUNCHED();
+    }
+    CUtensorMap ma, mb;
+    int s1 = make_map(&ma, kind, As, 2 * Mp, Kp, BM);
+    int s2 = make_map(&mb, kind, Bs, 2 * Np, Kp, bn);
+    if (s1 != TN_OK || s2 != TN_OK) { ar.release(mark); return TN_ECUDA; }
+    const int nkb = Kp / kq;
+    const int s = kind == 0 ? launch_tc<0>(st, ma, mb, Mp, Np, nkb, m, n, alpha, beta, C, ldc)
+                            : launch_tc<1>(st, ma, mb, Mp, Np, nkb, m, n, alpha, beta, C, ldc);
+    ar.release(mark);       // stream-ordered: later work on this stream may reuse the split buffers
+    return s;
+}
+
+int tc_status(cudaStream_t st, int* status)
+{
+    int v = 0;
+    TN_CUDA(cudaMemcpyFromSymbolAsync(&v, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    TN_CUDA(cudaStreamSynchronize(st));
+    *status = v;
+    if (v) {
+        const int zero = 0;
+        TN_CUDA(cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+    }
+    return TN_OK;
+}
+
+}  // namespace tn

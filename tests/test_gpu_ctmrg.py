@@ -85,7 +85,11 @@ def test_converged_corner_spectra(D, chi):
     for i, (x, y) in enumerate([(0, 0), (1, 0), (0, 1), (1, 1)]):
         for c in range(4):
             np.testing.assert_allclose(sp[i, c], ref[(x, y, 'C%d' % (c + 1))], atol=1e-9)
-    assert abs(rep['iterations'] - it) <= 2     # the stopping test may fire one iteration apart
+    # Near the stop the delta falls by only a factor of ~3 per iteration and in plateaus
+    # (3.2e-11, 2.5e-11, 1.1e-11 for this seed at tol 1e-11), so rounding-level
+    # differences in the spectra can move the stop by a few iterations.
+    assert rep['converged'] and conv
+    assert abs(rep['iterations'] - it) <= 4
     ctx.close()
 
 
