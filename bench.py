@@ -3,13 +3,17 @@
 
 Workload (one "step"): one full-update imaginary-time step of the 2D
 transverse-field Ising model (h = 3.04, tau = 0.005) on the 2-site
-checkerboard iPEPS, D = 4, chi = 64, FP64:
+checkerboard iPEPS, D = 4, chi = 64:
   canonical form + iPEPO + simple-update pre-truncation + double layers,
   a warm-started CTMRG budget of CTM_ITERS iterations (4 directional moves each),
   bond environments + ALS + assembly of every link type.
-The CTMRG budget is fixed so that every implementation does the same work per
-step; the energy error against the FP64 oracle is measured on the converged
-D = 2, chi = 8 workload and reported beside the throughput.
+The headline is the precision form (CTMRG contractions as TF32x3 products on
+the tensor cores; projector SVD, bond environment, ALS, gauge fixing in FP64);
+the plain FP64 form and the BF16x3 form are timed on the same steps and
+reported beside it.  The CTMRG budget is fixed so that every implementation
+does the same work per step.  Energy errors: each form's evolved D = 4,
+chi = 64 state against the FP64 form's, and the converged D = 2, chi = 8
+workload against the FP64 oracle.
 
 Prints one JSON line.  --impl reference times the CPU oracle on the same
 workload (a bounded sample, scaled to steps/s).
@@ -32,6 +36,8 @@ CTM_ITERS = 4
 MOVES_PER_STEP = 4 * CTM_ITERS
 N_RE = 5                            # recycled steps per environment computation (Sec. VI.C)
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (SIMT) at the 2070 MHz boost clock
+TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor rate
+PRECISIONS = {"f64": 0, "tf32x3": 1, "bf16x3": 2}
 
 
 def parse():
@@ -42,6 +48,7 @@ def parse():
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--profile-moves", type=int, default=0,
                    help="run only this many CTMRG moves and one update at the workload shape (for ncu)")
+    p.add_argument("--profile-precision", default="tf32x3", choices=sorted(PRECISIONS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -170,9 +177,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "moves_per_s": 1.0 / t_move,
-        "config": dict(workload="ITE full-update step, 2D TFIM h=3.04 tau=0.005, checkerboard iPEPS D=4 chi=64, "
-                                "CTMRG budget %d iterations per step" % CTM_ITERS, **WL,
-                       ctm_iterations_per_step=CTM_ITERS),
+        "config": workload_config(1),
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads_used(), "kind": "oracle",
                          "sample": samples[0]["sample"]},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -181,30 +186,111 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-def energy_error_small():
+def energy_error_small(L, precision):
     """|E_gpu - E_oracle| / |E| after 3 plain steps of the D=2, chi=8 workload (h=3, tau=0.01)."""
     from oracle import ctmrg as OC
     from oracle import recycle as OR
-    from paper_1411_0391_gb300 import _lib as L
     from paper_1411_0391_gb300.inputs import random_peps
     D, chi, h, tau = 2, 8, 3.0, 0.01
     A = random_peps(2, D)
-    ctx = L.Context(D, chi)
+    ctx = L.Context(D, chi, precision=precision)
     ctx.tn_set_hamiltonian(1.0, h)
     ctx.tn_set_time_step(tau)
     ctx.tn_set_state(A)
     cfg = OR.Config(h=h, tau=tau, D=D, chi=chi, ctm_tol=1e-10, ctm_max=500)
+    ctm_tol = 1e-10 if precision == L.TN_F64 else 1e-8
     env, Ao = None, A
     for _ in range(3):
-        ctx.tn_fu_step(1e-10, 500)
+        ctx.tn_fu_step(ctm_tol, 500)
         Ao, env, _ = OR.fu_step(Ao, OC.checkerboard(), cfg, env)
     ctx.tn_build_double_layer()
     ctx.tn_reset_env()
-    ctx.tn_ctmrg(1e-12, 500)
+    ctx.tn_ctmrg(1e-12 if precision == L.TN_F64 else 1e-8, 500)
     g = ctx.tn_measure()
     o = OR.energy(Ao, OC.checkerboard(), cfg, tol=1e-12)
     ctx.close()
     return abs(g["e_site"] - o["e_site"]) / abs(o["e_site"]), g["e_site"], o["e_site"]
+
+
+def time_form(L, torch, dev, stream, precision, state, args, flush):
+    """Warm-up, then args.steps timed plain steps and args.steps recycled windows of one precision form."""
+    D, chi = WL["D"], WL["chi"]
+    ctx = L.Context(D, chi, device=dev, precision=precision)
+    ctx.tn_set_hamiltonian(1.0, WL["h"])
+    ctx.tn_set_time_step(WL["tau"])
+    ctx.tn_set_state(state)
+    for _ in range(args.warmup):
+        ctx.tn_step_prepare()
+        ctx.tn_ctmrg(0.0, CTM_ITERS)
+        ctx.tn_step_update()
+    t_prep = t_ctm = t_upd = 0.0
+    launches = svd_calls = svd_iters = 0
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        l0 = L.tn_launch_count()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        ctx.tn_step_prepare()
+        ev[1].record(stream)
+        rep = ctx.tn_ctmrg(0.0, CTM_ITERS)
+        ev[2].record(stream)
+        svd_calls += rep["svd_calls"]
+        svd_iters += rep["svd_iterations"]
+        ctx.tn_step_update()
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        launches += L.tn_launch_count() - l0
+        t_prep += ev[0].elapsed_time(ev[1]) / 1e3
+        t_ctm += ev[1].elapsed_time(ev[2]) / 1e3
+        t_upd += ev[2].elapsed_time(ev[3]) / 1e3
+    # recycled form (Sec. VI.C): one environment computation, then N_RE steps with the renormalised gate
+    t_rec = 0.0
+    F = None
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.tn_step_prepare()
+        ctx.tn_ctmrg(0.0, CTM_ITERS)
+        ctx.tn_step_update()
+        F = ctx.tn_recycle(N_RE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_rec += e0.elapsed_time(e1) / 1e3
+    total = t_prep + t_ctm + t_upd
+    return ctx, dict(total=total, t_prep=t_prep, t_ctm=t_ctm, t_upd=t_upd, launches=launches,
+                     svd_calls=svd_calls, svd_iters=svd_iters, t_rec=t_rec, fidelity=F)
+
+
+def form_summary(r, steps, world):
+    return {"steps_per_s": world * steps / r["total"], "moves_per_s": world * steps * MOVES_PER_STEP / r["t_ctm"],
+            "time_split_s": {"prepare": r["t_prep"], "ctmrg": r["t_ctm"], "update": r["t_upd"]},
+            "projector_svd": {"calls": r["svd_calls"], "iterations_per_call": r["svd_iters"] / max(r["svd_calls"], 1)},
+            "recycled": {"n_re": N_RE, "steps_per_s": world * steps * N_RE / r["t_rec"],
+                         "speedup_vs_plain": (steps * N_RE / r["t_rec"]) / (steps / r["total"]),
+                         "last_fidelity": r["fidelity"]}}
+
+
+def full_size_energy(ctx, iters):
+    """E_site of the evolved state: fresh double layer, warm CTMRG for `iters` iterations, measure."""
+    ctx.tn_build_double_layer()
+    ctx.tn_ctmrg(0.0, iters)
+    return ctx.tn_measure()
+
+
+def kernel_time(torch, stream, fn, reps=10):
+    for _ in range(3):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
 
 
 def run_gpu(args):
@@ -225,78 +311,53 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     D, chi = WL["D"], WL["chi"]
-    ctx = L.Context(D, chi, device=dev)
-    ctx.tn_set_hamiltonian(1.0, WL["h"])
-    ctx.tn_set_time_step(WL["tau"])
     state = random_peps(2, D, instance=rank)          # replicas: independent instances per rank
-    ctx.tn_set_state(state)
 
     if args.profile_moves:
+        ctx = L.Context(D, chi, device=dev, precision=PRECISIONS[args.profile_precision])
+        ctx.tn_set_hamiltonian(1.0, WL["h"])
+        ctx.tn_set_time_step(WL["tau"])
+        ctx.tn_set_state(state)
         ctx.tn_step_prepare()
         ctx.tn_ctmrg_moves(args.profile_moves)
         ctx.tn_step_update()
         torch.cuda.synchronize()
-        print(json.dumps({"profile_moves": args.profile_moves, "launches": L.tn_launch_count()}))
+        print(json.dumps({"profile_moves": args.profile_moves, "precision": args.profile_precision,
+                          "launches": L.tn_launch_count()}))
         return
 
-    for _ in range(args.warmup):
-        ctx.tn_step_prepare()
-        ctx.tn_ctmrg(0.0, CTM_ITERS)
-        ctx.tn_step_update()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)       # larger than the 129 MB L2
-    t_prep = t_ctm = t_upd = 0.0
-    launches = 0
-    svd_calls = svd_iters = 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    results, ctxs = {}, {}
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            l0 = L.tn_launch_count()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            ev[0].record(stream)
-            ctx.tn_step_prepare()
-            ev[1].record(stream)
-            rep = ctx.tn_ctmrg(0.0, CTM_ITERS)
-            ev[2].record(stream)
-            svd_calls += rep["svd_calls"]
-            svd_iters += rep["svd_iterations"]
-            ctx.tn_step_update()
-            ev[3].record(stream)
-            torch.cuda.synchronize()
-            launches += L.tn_launch_count() - l0
-            t_prep += ev[0].elapsed_time(ev[1]) / 1e3
-            t_ctm += ev[1].elapsed_time(ev[2]) / 1e3
-            t_upd += ev[2].elapsed_time(ev[3]) / 1e3
-    total = t_prep + t_ctm + t_upd
+        for name in ("tf32x3", "f64", "bf16x3"):
+            ctxs[name], results[name] = time_form(L, torch, dev, stream, PRECISIONS[name], state, args, flush)
+    head = results["tf32x3"]
+    total, t_ctm = head["total"], head["t_ctm"]
     if dist:
         t = torch.tensor([total, t_ctm], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total, t_ctm = float(t[0]), float(t[1])
     value = world * args.steps / total
-    moves_per_s = world * args.steps * MOVES_PER_STEP / t_ctm
 
-    # recycled form (Sec. VI.C): one environment computation, then N_RE steps with the renormalised gate
-    t_rec = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.tn_step_prepare()
-        ctx.tn_ctmrg(0.0, CTM_ITERS)
-        ctx.tn_step_update()
-        F = ctx.tn_recycle(N_RE)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_rec += e0.elapsed_time(e1) / 1e3
-    recycled = {"n_re": N_RE, "steps_per_s": world * args.steps * N_RE / t_rec,
-                "speedup_vs_plain": (args.steps * N_RE / t_rec) / (args.steps / total), "last_fidelity": F}
+    import numpy as np
+    # energy at full size.  (1) The environment's precision alone: the FP64 form's evolved state,
+    # loaded into every form, CTMRG converged (warm) in that form, measured in FP64.
+    # (2) Trajectory: each form's own evolved state after the same steps, same CTMRG budget.
+    energies_traj = {name: full_size_energy(ctxs[name], 8)["e_site"] for name in ctxs}
+    ref_state = [np.ascontiguousarray(a) for a in ctxs["f64"].tn_get_state()]
+    energies = {}
+    for name in ctxs:
+        ctxs[name].tn_set_state(ref_state)
+        ctxs[name].tn_build_double_layer()
+        ctxs[name].tn_ctmrg(1e-9 if name == "f64" else 1e-7, 60)
+        energies[name] = ctxs[name].tn_measure()["e_site"]
+    e_ref = energies["f64"]
 
     # end to end through the public API with host buffers: H2D of the state, the step, D2H of the result
-    import numpy as np
+    ctx = ctxs["tf32x3"]
     host = [np.ascontiguousarray(a) for a in ctx.tn_get_state()]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -310,60 +371,90 @@ def run_gpu(args):
     e2e_t = time.perf_counter() - t0
     state_bytes = sum(a.nbytes for a in host)
 
-    # roofline of the dominant kernel: the FP64 GEMM of the N x N half-system and loop products
+    # kernels of the N x N products: FP64 SIMT GEMM and the tcgen05 split-precision GEMM
     N = chi * D * D
     A = torch.randn(N, N, dtype=torch.float64, device=dev)
     B = torch.randn(N, N, dtype=torch.float64, device=dev)
     C = torch.empty(N, N, dtype=torch.float64, device=dev)
-    for _ in range(3):
-        L.tn_gemm_f64(0, 0, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, 0, 1, stream)
-    reps = 10
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        L.tn_gemm_f64(0, 0, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, 0, 1, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_gemm = e0.elapsed_time(e1) / 1e3 / reps
-    achieved = 2.0 * N ** 3 / t_gemm / 1e12
+    work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_TF32X3, N, N, N), dtype=torch.uint8, device=dev)
+    t_dgemm = kernel_time(torch, stream, lambda: L.tn_gemm_f64(0, 0, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, 0, 1,
+                                                              stream))
+    t_tc = kernel_time(torch, stream, lambda: L.tn_gemm_split(L.TN_TF32X3, 0, 0, N, N, N, 1.0, A, N, B, N, 0.0, C, N,
+                                                             work, stream))
     csum = clk.summary()
     sm_mhz = csum.get("sm_mhz") or 2070.0
-    peak = FP64_NOMINAL_TFLOPS * sm_mhz / 2070.0
+    fp64_peak = FP64_NOMINAL_TFLOPS * sm_mhz / 2070.0
+    peaks = measured_peaks()
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
 
     if rank != 0:
         return
+    fsum = {name: form_summary(results[name], args.steps, world) for name in results}
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "moves_per_s": moves_per_s,
-        "time_split_s": {"prepare": t_prep, "ctmrg": t_ctm, "update": t_upd},
-        "projector_svd": {"calls": svd_calls, "iterations_per_call": svd_iters / max(svd_calls, 1)},
-        "recycled": recycled,
-        "config": dict(workload="ITE full-update step, 2D TFIM h=3.04 tau=0.005, checkerboard iPEPS D=4 chi=64, "
-                                "CTMRG budget %d iterations per step" % CTM_ITERS, **WL,
-                       ctm_iterations_per_step=CTM_ITERS, parallelism="replicas" if world > 1 else "single",
-                       l2="flushed between timed steps (256 MB write)"),
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3+f64", "data": "synthetic",
+        "moves_per_s": world * args.steps * MOVES_PER_STEP / t_ctm,
+        "time_split_s": fsum["tf32x3"]["time_split_s"],
+        "projector_svd": fsum["tf32x3"]["projector_svd"],
+        "recycled": fsum["tf32x3"]["recycled"],
+        "forms": {"f64": fsum["f64"], "bf16x3": fsum["bf16x3"]},
+        "speedup_vs_f64": {"steps": fsum["tf32x3"]["steps_per_s"] / fsum["f64"]["steps_per_s"],
+                           "moves": fsum["tf32x3"]["moves_per_s"] / fsum["f64"]["moves_per_s"],
+                           "recycled_steps_vs_plain_f64": fsum["tf32x3"]["recycled"]["steps_per_s"]
+                           / fsum["f64"]["steps_per_s"]},
+        "config": workload_config(world),
         "e2e": {"value": world * args.steps / e2e_t, "unit": "steps/s", "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(head["launches"]),
         "clocks": csum,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "dgemm_kernel %dx%dx%d (FP64 SIMT; GB300 has no FP64 tensor path)"
-                     % (N, N, N), "peak_source": "derived: 1.25 TFLOP/s FP64 at 2070 MHz scaled to the median "
-                     "sampled SM clock"},
+        "roofline": {"bound": "alu", "achieved": 2.0 * N ** 3 / t_dgemm / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": 2.0 * N ** 3 / t_dgemm / 1e12 / fp64_peak, "traffic": None,
+                     "kernel": "dgemm_kernel %dx%dx%d (FP64 SIMT; GB300 has no FP64 tensor path)" % (N, N, N),
+                     "peak_source": "derived: 1.25 TFLOP/s FP64 at 2070 MHz scaled to the median sampled SM clock"},
+        "roofline_tensor": {"bound": "tensor", "kernel": "tc_gemm_kernel TF32x3 %dx%dx%d incl. operand split" % (N, N, N),
+                            "achieved": 3 * 2.0 * N ** 3 / t_tc / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                            "frac": 3 * 2.0 * N ** 3 / t_tc / 1e12 / tf32_peak, "traffic": None,
+                            "peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32:BF16 dense ratio), of measured",
+                            "ms": t_tc * 1e3, "f64_dgemm_ms": t_dgemm * 1e3},
+        "energy_err": {"full_size_vs_f64": {name: abs(energies[name] - e_ref) / abs(e_ref) for name in energies
+                                            if name != "f64"},
+                       "full_size_e_site": energies,
+                       "full_size_workload": "D=4 chi=64: the FP64 form's evolved state; CTMRG converged in each form "
+                                             "(warm, tol 1e-9 FP64 / 1e-7 split, cap 60 iterations); observables FP64",
+                       "trajectory_vs_f64": {name: abs(energies_traj[name] - energies_traj["f64"])
+                                             / abs(energies_traj["f64"]) for name in energies_traj if name != "f64"},
+                       "trajectory_workload": "each form's own state after the bench's steps (same schedule from the "
+                                              "same start), 8 warm CTMRG iterations, measured in FP64"},
     }
-    try:
-        err, eg, eo = energy_error_small()
-        line["energy_err"] = {"rel": err, "workload": "D=2 chi=8 h=3 tau=0.01, 3 plain steps, CTMRG tol 1e-10",
-                              "e_gpu": eg, "e_oracle": eo}
-    except Exception as ex:                                 # reported, never hidden
-        line["energy_err"] = {"error": repr(ex)}
+    for name, prec in (("f64", L.TN_F64), ("tf32x3", L.TN_TF32X3)):
+        try:
+            err, eg, eo = energy_error_small(L, prec)
+            line["energy_err"]["vs_oracle_" + name] = {"rel": err, "e_gpu": eg, "e_oracle": eo,
+                                                       "workload": "D=2 chi=8 h=3 tau=0.01, 3 plain steps"}
+        except Exception as ex:                                 # reported, never hidden
+            line["energy_err"]["vs_oracle_" + name] = {"error": repr(ex)}
     if world == 1 and not args.no_cpu_baseline:
         s = oracle_sample()
         line["cpu_baseline"] = {"value": 1.0 / s["t_step"], "unit": "steps/s", "cores": threads_used(),
                                 "kind": "oracle", "sample": s["sample"], "moves_per_s": 1.0 / s["t_move"]}
     print(json.dumps(line))
+
+
+def workload_config(world):
+    return dict(workload="ITE full-update step, 2D TFIM h=3.04 tau=0.005, checkerboard iPEPS D=4 chi=64, "
+                         "CTMRG budget %d iterations per step; precision form: CTMRG contractions TF32x3 on "
+                         "tensor cores, projector SVD / bond environment / ALS / gauge fix FP64" % CTM_ITERS,
+                **WL, ctm_iterations_per_step=CTM_ITERS, parallelism="replicas" if world > 1 else "single",
+                l2="flushed between timed steps (256 MB write)")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
 
 
 def main():

@@ -60,7 +60,12 @@ typedef struct tn_config {
     int D;          /* PEPS bond dimension, 1..8 */
     int chi;        /* CTM bond dimension, 1 <= chi <= 96 */
     int cell;       /* TN_CELL_CHECKERBOARD or TN_CELL_SINGLE */
-    int precision;  /* TN_F64 */
+    int precision;  /* arithmetic of the CTMRG contractions (enlarged corners,
+                       half-system products, products of the projector SVD,
+                       renormalisation): TN_F64, TN_TF32X3 or TN_BF16X3.  The
+                       small factorisations, the bond environment, the
+                       full-update solve, gauge fixing and observables are
+                       FP64 in every mode. */
 } tn_config;
 
 /* Number of kernels this library has launched in the process so far (all
@@ -260,7 +265,7 @@ int tn_truncated_svd(void* ctx, const double* dM, int m, int k, double* dU, doub
  * that must not take the device-wide synchronisation of cudaMalloc/cudaFree,
  * or a plugin without a context workspace -- it takes only the caller's
  * buffers (dM: m x m input, dU/dV: m x k, dS: k, warm: optional m x k start)
- * and uses a fixed device array of 2^19 doubles (4 MiB) that the library
+ * and uses a fixed device array of 2^20 doubles (8 MiB) that the library
  * reserves on every GPU that loads it, until the process exits.
  *  - Limits: k <= 96 and k <= m; the (m, k) scratch need must fit the array
  *    (e.g. m <= 1024 with k <= 64 fits; m <= 112 always fits), otherwise

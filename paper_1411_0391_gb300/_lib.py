@@ -182,7 +182,7 @@ def tn_truncated_svd(ctx, M, m, k, U, S, V, warm=None):
 
 
 def tn_truncated_svd_noalloc(M, m, k, U, S, V, warm=None, stream=None):
-    """Allocation-free truncated SVD: only the caller's buffers, fixed 4 MiB library scratch."""
+    """Allocation-free truncated SVD: only the caller's buffers, fixed 8 MiB library scratch."""
     return _check(lib().tn_truncated_svd_noalloc(c_void_p(M.data_ptr()), m, k, c_void_p(U.data_ptr()),
                                                  c_void_p(S.data_ptr()), c_void_p(V.data_ptr()),
                                                  c_void_p(0 if warm is None else warm.data_ptr()),
@@ -195,9 +195,9 @@ def tn_truncated_svd_noalloc(M, m, k, U, S, V, warm=None, stream=None):
 class Context:
     """One tnite context: its device workspace is a torch uint8 tensor on `device`."""
 
-    def __init__(self, D, chi, cell=TN_CELL_CHECKERBOARD, device="cuda:0", stream=None):
+    def __init__(self, D, chi, cell=TN_CELL_CHECKERBOARD, device="cuda:0", stream=None, precision=TN_F64):
         import torch
-        self.cfg = tn_config(D, chi, cell, TN_F64)
+        self.cfg = tn_config(D, chi, cell, precision)
         nbytes = lib().tn_workspace_bytes(byref(self.cfg))
         if nbytes == 0:
             raise TnError(TN_EINVAL, "tn_workspace_bytes")

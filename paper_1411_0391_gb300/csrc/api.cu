@@ -27,7 +27,7 @@ static bool valid_cfg(const tn_config* cfg)
     if (cfg->D < 1 || cfg->D > 6) return false;
     if (cfg->chi < 1 || cfg->chi > 96) return false;
     if (cfg->cell != TN_CELL_CHECKERBOARD && cfg->cell != TN_CELL_SINGLE) return false;
-    if (cfg->precision != TN_F64) return false;
+    if (cfg->precision != TN_F64 && cfg->precision != TN_TF32X3 && cfg->precision != TN_BF16X3) return false;
     return true;
 }
 

@@ -3,46 +3,48 @@
 //
 // GB300 executes FP64 on the SIMT pipe only (no FP64 tensor-core path), at a
 // rate far below its memory bandwidth, so the GEMM is a register-tiled SIMT
-// kernel whose only job is to keep the FP64 units busy: 64x64 output tiles,
-// 16-deep k slices staged in shared memory, 4x4 outputs per thread.
+// kernel whose only job is to keep the FP64 units busy: 64x64 output tiles
+// (32x32 or 16x16 when the product has few tiles), 16-deep k slices staged in
+// shared memory, 4x4 (2x2, 1x1) outputs per thread.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace tn {
 
-constexpr int GT = 64;     // tile edge
 constexpr int GK = 16;     // k slice
 
-template <bool TA, bool TB>
+// T x T output tile per block of 256 threads, (T/16) x (T/16) outputs per thread.
+template <int T, bool TA, bool TB>
 __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double alpha,
         const double* __restrict__ A, int lda, long long sA,
         const double* __restrict__ B, int ldb, long long sB, double beta,
         double* __restrict__ C, int ldc, long long sC)
 {
-    __shared__ double As[GK][GT + 1];
-    __shared__ double Bs[GK][GT + 1];
+    constexpr int R = T / 16;
+    __shared__ double As[GK][T + 1];
+    __shared__ double Bs[GK][T + 1];
     const int b = blockIdx.z;
     A += b * sA; B += b * sB; C += b * sC;
-    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+    const int row0 = blockIdx.y * T, col0 = blockIdx.x * T;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4];
+    double acc[R][R];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
 
     for (int k0 = 0; k0 < k; k0 += GK) {
-        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+        for (int e = threadIdx.x; e < T * GK; e += 256) {
             int r, kk;
-            if (TA) { r = e % GT; kk = e / GT; } else { kk = e % GK; r = e / GK; }
+            if (TA) { r = e % T; kk = e / T; } else { kk = e % GK; r = e / GK; }
             int gr = row0 + r, gk = k0 + kk;
             double v = 0.0;
             if (gr < m && gk < k) v = TA ? A[(long long)gk * lda + gr] : A[(long long)gr * lda + gk];
             As[kk][r] = v;
         }
-        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+        for (int e = threadIdx.x; e < T * GK; e += 256) {
             int c, kk;
-            if (TB) { kk = e % GK; c = e / GK; } else { c = e % GT; kk = e / GT; }
+            if (TB) { kk = e % GK; c = e / GK; } else { c = e % T; kk = e / T; }
             int gc = col0 + c, gk = k0 + kk;
             double v = 0.0;
             if (gc < n && gk < k) v = TB ? B[(long long)gc * ldb + gk] : B[(long long)gk * ldb + gc];
@@ -51,30 +53,53 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int m, int n, int k, double 
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            double a[4], bb[4];
+            double a[R], bb[R];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < R; ++j) bb[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+                for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
         int r = row0 + ty + 16 * i;
         if (r >= m) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
             int c = col0 + tx + 16 * j;
             if (c >= n) continue;
             double* dst = C + (long long)r * ldc + c;
             *dst = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*dst);
         }
     }
+}
+
+template <int T>
+static void launch_dgemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
+                         const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
+                         double beta, double* C, int ldc, long long sC, int batch)
+{
+    dim3 grid((n + T - 1) / T, (m + T - 1) / T, batch);
+    if (!ta && !tb) dgemm_kernel<T, false, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else if (ta && !tb) dgemm_kernel<T, true, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else if (!ta && tb) dgemm_kernel<T, false, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else dgemm_kernel<T, true, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+}
+
+// Tile edge: 64 while that gives a full wave of blocks, else smaller tiles so
+// that few-tile products (n <= 112 panels and square blocks) still spread over
+// many SMs -- each SM has little FP64 throughput of its own.
+static int gemm_tile(int m, int n, int batch)
+{
+    auto blocks = [&](int t) { return (long long)((m + t - 1) / t) * ((n + t - 1) / t) * batch; };
+    if (blocks(64) >= 152) return 64;
+    if (blocks(32) >= 152) return 32;
+    return 16;
 }
 
 int gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
@@ -89,14 +114,20 @@ int gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
         return TN_OK;
     }
     if (batch > 65535) return TN_EINVAL;
-    dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, batch);
-    if (grid.y > 65535) return TN_EINVAL;
-    if (!ta && !tb) dgemm_kernel<false, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
-    else if (ta && !tb) dgemm_kernel<true, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
-    else if (!ta && tb) dgemm_kernel<false, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
-    else dgemm_kernel<true, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    const int t = gemm_tile(m, n, batch);
+    if ((m + t - 1) / t > 65535) return TN_EINVAL;
+    if (t == 64) launch_dgemm<64>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+    else if (t == 32) launch_dgemm<32>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+    else launch_dgemm<16>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
     TN_LAUNCHED();
     return TN_OK;
+}
+
+int gemm_any(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,
+             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc)
+{
+    if (kind >= 0) return gemm_tc(st, ar, kind, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    return gemm(st, ta, tb, m, n, k, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -121,7 +152,7 @@ __global__ void splitk_reduce_kernel(const double* __restrict__ P, int splits, i
 int gemm_splitk(cudaStream_t st, Arena& ar, bool ta, bool tb, int m, int n, int k, double alpha,
                 const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc)
 {
-    const int tiles = ((m + GT - 1) / GT) * ((n + GT - 1) / GT);
+    const int tiles = ((m + 63) / 64) * ((n + 63) / 64);
     int splits = 1;
     if (tiles < 152 && k >= 256) splits = std::min(std::max(1, 304 / tiles), std::max(1, k / 128));
     if (splits <= 1) return gemm(st, ta, tb, m, n, k, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1);

@@ -43,7 +43,7 @@ int permute_spec(cudaStream_t st, const char* spec, const DT& in, const DT& out)
 }
 
 int contract(cudaStream_t st, Arena& ar, const char* spec, const DT& A, const DT& B, const DT& C,
-             double alpha, double beta)
+             double alpha, double beta, int kind)
 {
     Spec s;
     if (!parse(spec, s)) return TN_EINVAL;
@@ -110,12 +110,12 @@ int contract(cudaStream_t st, Arena& ar, const char* spec, const DT& A, const DT
     const int lda = ta ? (int)M : (int)K;
     const int ldb = tb ? (int)K : (int)N;
     if (s.c == fa + fb) {
-        TN_TRY(gemm(st, ta, tb, (int)M, (int)N, (int)K, alpha, pA, lda, 0, pB, ldb, 0, beta, C.p, (int)N, 0, 1));
+        TN_TRY(gemm_any(st, ar, kind, ta, tb, (int)M, (int)N, (int)K, alpha, pA, lda, pB, ldb, beta, C.p, (int)N));
     } else {
         if (beta != 0.0) { ar.release(mk); return TN_EINVAL; }
         double* t = ar.take((size_t)M * N);
         if (!t) { ar.release(mk); return TN_ENOMEM; }
-        TN_TRY(gemm(st, ta, tb, (int)M, (int)N, (int)K, alpha, pA, lda, 0, pB, ldb, 0, 0.0, t, (int)N, 0, 1));
+        TN_TRY(gemm_any(st, ar, kind, ta, tb, (int)M, (int)N, (int)K, alpha, pA, lda, pB, ldb, 0.0, t, (int)N));
         DT o; o.p = t; o.rank = (int)(fa.size() + fb.size());
         std::string have = fa + fb;
         for (int j = 0; j < o.rank; ++j) o.dim[j] = dim[(unsigned char)have[j]];

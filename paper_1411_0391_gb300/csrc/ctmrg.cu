@@ -122,14 +122,15 @@ static int enlarged_corner(Ctx& c, const Env& e, int k, const double* ab, double
     const double* C = e.C[k];
     const double* Ta = e.T[k];
     const double* Tb = e.T[(k + 3) & 3];
+    const int kd = c.kind();
     // X[o, j, n] = C[o, a] Ta[a, j, n]
-    TN_TRY(gemm(c.st, false, false, chi, chi * L, chi, 1.0, C, chi, 0, Ta, chi * L, 0, 0.0, X, chi * L, 0, 1));
+    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, chi, chi * L, chi, 1.0, C, chi, Ta, chi * L, 0.0, X, chi * L));
     // Y[i, m, j, n] = Tb[i, o, m] X[o, j, n]
     TN_TRY(contract(c.st, c.ar, "iom,ojn->imjn", dt((double*)Tb, {chi, chi, L}), dt(X, {chi, chi, L}),
-                    dt(Y, {chi, L, chi, L})));
+                    dt(Y, {chi, L, chi, L}), 1.0, 0.0, kd));
     // Q[i, r, j, q] = Y[i, m, j, n] ab[m, n, r, q]
     TN_TRY(contract(c.st, c.ar, "imjn,mnrq->irjq", dt(Y, {chi, L, chi, L}), dt((double*)ab, {L, L, L, L}),
-                    dt(Q, {chi, L, chi, L})));
+                    dt(Q, {chi, L, chi, L}), 1.0, 0.0, kd));
     c.ar.release(mk);
     return TN_OK;
 }
@@ -153,23 +154,26 @@ static int cut_projectors(Ctx& c, Frame& f, int x, int y, double* Pup, double* P
     double* U = c.ar.take((size_t)N * chi);
     double* S = c.ar.take(chi);
     if (!Ru || !Rd || !rho || !U || !S) return TN_ENOMEM;
-    TN_TRY(gemm(c.st, false, false, N, N, N, 1.0, Q[0], N, 0, Q[1], N, 0, 0.0, Ru, N, 0, 1));
-    TN_TRY(gemm(c.st, false, false, N, N, N, 1.0, Q[2], N, 0, Q[3], N, 0, 0.0, Rd, N, 0, 1));
-    TN_TRY(gemm(c.st, false, false, N, N, N, 1.0, Rd, N, 0, Ru, N, 0, 0.0, rho, N, 0, 1));
+    const int kd = c.kind();
+    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, N, N, N, 1.0, Q[0], N, Q[1], N, 0.0, Ru, N));
+    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, N, N, N, 1.0, Q[2], N, Q[3], N, 0.0, Rd, N));
+    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, N, N, N, 1.0, Rd, N, Ru, N, 0.0, rho, N));
     const int xx = ((x % f.Lx) + f.Lx) % f.Lx, yy = ((y % f.Ly) + f.Ly) % f.Ly;
     double* Vw = c.warmV[f.rot][xx][yy];
     // V goes straight into the warm-start slot of this cut
     TsvdStats stats;
-    int s = truncated_svd(c.st, c.ar, rho, N, chi, U, S, Vw, c.warm_ok[f.rot][xx][yy] ? Vw : nullptr, &stats);
+    // the projector SVD runs in FP64 in every mode (products with rho included)
+    int s = truncated_svd(c.st, c.ar, rho, N, chi, U, S, Vw, c.warm_ok[f.rot][xx][yy] ? Vw : nullptr, &stats,
+                          -1, c.svd_tol());
     if (s != TN_OK && s != TN_ENOCONV) return s;
     c.svd_calls += 1;
     c.svd_iterations += stats.iterations;
     c.warm_ok[f.rot][xx][yy] = true;
     // P_up = R_d^T U S^{-1/2}, P_lo = R_u V S^{-1/2}
-    TN_TRY(gemm(c.st, true, false, N, chi, N, 1.0, Rd, N, 0, U, chi, 0, 0.0, Pup, chi, 0, 1));
-    TN_TRY(gemm(c.st, false, false, N, chi, N, 1.0, Ru, N, 0, Vw, chi, 0, 0.0, Plo, chi, 0, 1));
-    TN_TRY(scale_cols_invsqrt(c.st, Pup, N, chi, S, 1e-12));
-    TN_TRY(scale_cols_invsqrt(c.st, Plo, N, chi, S, 1e-12));
+    TN_TRY(gemm_any(c.st, c.ar, kd, true, false, N, chi, N, 1.0, Rd, N, U, chi, 0.0, Pup, chi));
+    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, N, chi, N, 1.0, Ru, N, Vw, chi, 0.0, Plo, chi));
+    TN_TRY(scale_cols_invsqrt(c.st, Pup, N, chi, S, c.proj_cut()));
+    TN_TRY(scale_cols_invsqrt(c.st, Plo, N, chi, S, c.proj_cut()));
     c.ar.release(mk);
     return TN_OK;
 }
@@ -187,22 +191,23 @@ static int renormalize(Ctx& c, Frame& f, int x, int y, const double* pu_above, c
     double* X2 = c.ar.take((size_t)chi * chi * L * L);
     double* TC = c.ar.take((size_t)chi * chi * L);
     if (!CT || !X1 || !X2 || !TC) return TN_ENOMEM;
+    const int kd = c.kind();
     // C1'[a, o] = P_up(y-1|y)[i, m, a] C1[i, c] T1[c, o, m]
-    TN_TRY(gemm(c.st, false, false, chi, chi * L, chi, 1.0, e.C[0], chi, 0, e.T[0], chi * L, 0, 0.0, CT, chi * L, 0, 1));
+    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, chi, chi * L, chi, 1.0, e.C[0], chi, e.T[0], chi * L, 0.0, CT, chi * L));
     TN_TRY(contract(c.st, c.ar, "ima,iom->ao", dt((double*)pu_above, {chi, L, chi}), dt(CT, {chi, chi, L}),
-                    dt(C1n, {chi, chi})));
+                    dt(C1n, {chi, chi}), 1.0, 0.0, kd));
     // T4'[a, b, r] = P_up(y|y+1)[i, s, a] T4[i, j, m] a[m, r, s, t] P_lo(y-1|y)[j, t, b]
     TN_TRY(contract(c.st, c.ar, "isa,ijm->sajm", dt((double*)pu, {chi, L, chi}), dt(e.T[3], {chi, chi, L}),
-                    dt(X1, {L, chi, chi, L})));
+                    dt(X1, {L, chi, chi, L}), 1.0, 0.0, kd));
     TN_TRY(contract(c.st, c.ar, "sajm,smrt->ajrt", dt(X1, {L, chi, chi, L}), dt(c.aT4[f.rot][t], {L, L, L, L}),
-                    dt(X2, {chi, chi, L, L})));
+                    dt(X2, {chi, chi, L, L}), 1.0, 0.0, kd));
     TN_TRY(contract(c.st, c.ar, "ajrt,jtb->abr", dt(X2, {chi, chi, L, L}), dt((double*)pl_above, {chi, L, chi}),
-                    dt(T4n, {chi, chi, L})));
+                    dt(T4n, {chi, chi, L}), 1.0, 0.0, kd));
     // C4'[i, a] = C4[c, q] T3[i, c, m] P_lo(y|y+1)[q, m, a]
     TN_TRY(contract(c.st, c.ar, "icm,cq->iqm", dt(e.T[2], {chi, chi, L}), dt(e.C[3], {chi, chi}),
-                    dt(TC, {chi, chi, L})));
+                    dt(TC, {chi, chi, L}), 1.0, 0.0, kd));
     TN_TRY(contract(c.st, c.ar, "iqm,qma->ia", dt(TC, {chi, chi, L}), dt((double*)pl, {chi, L, chi}),
-                    dt(C4n, {chi, chi})));
+                    dt(C4n, {chi, chi}), 1.0, 0.0, kd));
     TN_TRY(normalize_maxabs(c.st, C1n, (long long)chi * chi, 1, 0));
     TN_TRY(normalize_maxabs(c.st, T4n, (long long)chi * chi * L, 1, 0));
     TN_TRY(normalize_maxabs(c.st, C4n, (long long)chi * chi, 1, 0));

@@ -72,6 +72,18 @@ struct Ctx {
     std::vector<double> prev_spectra;
 
     int N() const { return chi * leg; }
+    // contraction arithmetic of the CTMRG moves: -1 FP64, 0 TF32 x3, 1 BF16 x3
+    int kind() const { return cfg.precision == TN_TF32X3 ? 0 : cfg.precision == TN_BF16X3 ? 1 : -1; }
+    // Ritz residual threshold (relative to s_1) of the FP64 projector SVD: the loop
+    // matrix of the precision form is itself known only to the accuracy of its
+    // split products (~1e-7 TF32 x3, ~4e-6 BF16 x3), so resolving it further
+    // than 1e-10 (1e-9) buys nothing
+    double svd_tol() const { return cfg.precision == TN_TF32X3 ? 1e-10 : cfg.precision == TN_BF16X3 ? 1e-9 : 1e-13; }
+    // inverse-square-root cutoff of the projectors (relative to s_1): singular
+    // values of the loop matrix below it are dropped.  1e-12 in FP64; in the
+    // precision form the loop matrix is known only to its product error, and
+    // directions below ~8x that error are noise that S^{-1/2} would amplify
+    double proj_cut() const { return cfg.precision == TN_TF32X3 ? 1e-6 : cfg.precision == TN_BF16X3 ? 3e-5 : 1e-12; }
     size_t env_size() const { return (size_t)nsites * (4 * (size_t)chi * chi + 4 * (size_t)chi * chi * leg); }
     Frame frame0();
 };

@@ -30,8 +30,15 @@ int sign_fix_cols(cudaStream_t st, double* U, double* V, int rows, int vrows, in
 int orth(cudaStream_t st, Arena& ar, double* Y, int rows, int cols);
 int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, bool shifted);
 int tsvd_columns(int m, int k);
+// mixed.cu: FP32 factorisations refined to FP64 by matrix products
+int orth_mixed(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, int fixes);
+int svd_mixed(cudaStream_t st, Arena& ar, const double* B, int n, double* U, double* S, double* V, int steps);
+
+// kind: arithmetic of the products with M (see gemm_any); tol: Ritz residual
+// stopping threshold relative to the largest singular value.
 int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
-                  double* U, double* S, double* V, const double* warm, TsvdStats* stats);
+                  double* U, double* S, double* V, const double* warm, TsvdStats* stats,
+                  int kind = -1, double tol = 1e-13);
 
 // tc_gemm.cu: split-precision products on the tensor cores (kind 0 = TF32 x3,
 // 1 = BF16 x3); tc_status reads and clears the device-side wait flag.
@@ -40,11 +47,15 @@ size_t gemm_tc_scratch_bytes(int kind, int m, int n, int k);
 int gemm_tc(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,
             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
 int tc_status(cudaStream_t st, int* status);
+// C = alpha op(A) op(B) + beta C (no batch) in the contraction arithmetic
+// `kind`: -1 = FP64 SIMT, 0 = TF32 x3 tensor cores, 1 = BF16 x3.
+int gemm_any(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,
+             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
 
 // contract.cu: C = alpha * A.B (+ beta C when no output permutation is needed),
 // einsum-style labels "ab,bcm->acm" (no traces, no batch labels).
 int contract(cudaStream_t st, Arena& ar, const char* spec, const DT& A, const DT& B, const DT& C,
-             double alpha = 1.0, double beta = 0.0);
+             double alpha = 1.0, double beta = 0.0, int kind = -1);
 // out = in with axes permuted by a label spec "abcd->cabd"
 int permute_spec(cudaStream_t st, const char* spec, const DT& in, const DT& out);
 

@@ -214,16 +214,22 @@ int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols
 // truncated SVD
 // ---------------------------------------------------------------------------
 // Top-k triplets of the m x m matrix M (row-major).  m <= SMALL_MAX: one-sided
-// Jacobi on M.  Otherwise subspace iteration on kk = k + max(8, k/4) columns:
+// Jacobi on M.  Otherwise subspace iteration on kk = k + max(16, 3k/4) columns
+// (at most 112; 112 for k = 64: on flat loop spectra the convergence factor per
+// iteration, (s_{kk+1}/s_k)^2, needs the wide oversampling):
 //   Y = orth(M Om), Z = orth(M^T Y), T = M Z, B = Y^T T = Ub Sb Vb^T,
 //   Ritz vectors U_r = Y Ub, V_r = Z Vb; the next basis is Om = V_r, so B is
 //   nearly diagonal from the second iteration on.  Stop when every kept Ritz
-//   pair has || M v_i - s_i u_i || = || T vb_i - s_i u_i || <= 1e-13 s_1 (an
-//   absolute test: directions at the noise floor pass it too), cap 16.
-// All products run as (split-K) GEMMs over the GPU; the kk x kk Cholesky and
-// SVD run in one block each.  No heap allocation: host data lives on the stack.
+//   pair has || M v_i - s_i u_i || = || T vb_i - s_i u_i || <= tol s_1 (an
+//   absolute test: directions at the noise floor pass it too; tol = 1e-13 in
+//   FP64, looser when the products with M run on the tensor cores), cap 16.
+// All products run as (split-K) GEMMs over the GPU.  The kk x kk
+// factorisations run in one block each: on the first iteration in FP64, later
+// in FP32 with FP64 refinement by products (orth_mixed, svd_mixed), falling
+// back to the FP64 Jacobi SVD if the residual stops decreasing.  No heap
+// allocation: host data lives on the stack.
 int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
-                  double* U, double* S, double* V, const double* warm, TsvdStats* stats)
+                  double* U, double* S, double* V, const double* warm, TsvdStats* stats, int kind, double tol)
 {
     if (k < 1 || k > m) return TN_EINVAL;
     size_t mk = ar.mark();
@@ -260,15 +266,25 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
     const int max_it = 16;
     int it = 0;
     bool conv = false;
+    bool exact_rr = false;          // Rayleigh-Ritz SVD by FP64 Jacobi instead of FP32 + refinement
+    double prev_worst = 0.0;
     for (it = 1; it <= max_it; ++it) {
         const bool first = (it == 1);
-        TN_TRY(gemm_splitk(st, ar, false, false, m, kk, m, 1.0, M, m, Om, kk, 0.0, Y, kk));
-        TN_TRY(orth2(st, ar, Y, T, m, kk, first));
-        TN_TRY(gemm_splitk(st, ar, true, false, m, kk, m, 1.0, M, m, Y, kk, 0.0, Z, kk));
-        TN_TRY(orth2(st, ar, Z, T, m, kk, first));
-        TN_TRY(gemm_splitk(st, ar, false, false, m, kk, m, 1.0, M, m, Z, kk, 0.0, T, kk));
+        if (kind >= 0) TN_TRY(gemm_tc(st, ar, kind, false, false, m, kk, m, 1.0, M, m, Om, kk, 0.0, Y, kk));
+        else TN_TRY(gemm_splitk(st, ar, false, false, m, kk, m, 1.0, M, m, Om, kk, 0.0, Y, kk));
+        // the first basis (random or warm) may be ill conditioned: FP64 shifted CholeskyQR3;
+        // afterwards the panels are near orthogonal and FP32 whitening + FP64 fixes suffice
+        if (first) TN_TRY(orth2(st, ar, Y, T, m, kk, true));
+        else TN_TRY(orth_mixed(st, ar, Y, T, m, kk, 2));
+        if (kind >= 0) TN_TRY(gemm_tc(st, ar, kind, true, false, m, kk, m, 1.0, M, m, Y, kk, 0.0, Z, kk));
+        else TN_TRY(gemm_splitk(st, ar, true, false, m, kk, m, 1.0, M, m, Y, kk, 0.0, Z, kk));
+        if (first) TN_TRY(orth2(st, ar, Z, T, m, kk, true));
+        else TN_TRY(orth_mixed(st, ar, Z, T, m, kk, 2));
+        if (kind >= 0) TN_TRY(gemm_tc(st, ar, kind, false, false, m, kk, m, 1.0, M, m, Z, kk, 0.0, T, kk));
+        else TN_TRY(gemm_splitk(st, ar, false, false, m, kk, m, 1.0, M, m, Z, kk, 0.0, T, kk));
         TN_TRY(gemm_splitk(st, ar, true, false, kk, kk, m, 1.0, Y, kk, T, kk, 0.0, B, kk));
-        TN_TRY(svd_small(st, B, kk, kk, 1, Ub, Sb, Vb));
+        if (exact_rr) TN_TRY(svd_small(st, B, kk, kk, 1, Ub, Sb, Vb));
+        else TN_TRY(svd_mixed(st, ar, B, kk, Ub, Sb, Vb, 2));
         TN_TRY(gemm(st, false, false, m, k, kk, 1.0, Y, kk, 0, Ub, kk, 0, 0.0, Ur, k, 0, 1));     // U_r
         TN_TRY(gemm(st, false, false, m, k, kk, 1.0, T, kk, 0, Vb, kk, 0, 0.0, TV, k, 0, 1));     // M V_r
         TN_TRY(residual_norms(st, TV, k, Ur, k, Sb, m, k, rn));
@@ -278,7 +294,11 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
         TN_CUDA(cudaStreamSynchronize(st));
         double worst = 0.0;
         for (int i = 0; i < k; ++i) worst = std::max(worst, hr[i]);
-        if (worst <= 1e-13 * std::max(hs[0], 1e-300)) { conv = true; break; }
+        if (worst <= tol * std::max(hs[0], 1e-300)) { conv = true; break; }
+        // a residual that stopped falling may be the FP32 Jacobi's unresolved
+        // near-degenerate pairs: take the exact FP64 Ritz SVD from here on
+        if (!first && worst > 0.5 * prev_worst) exact_rr = true;
+        prev_worst = worst;
     }
     if (it > max_it) it = max_it;
     TN_CUDA(cudaMemcpyAsync(U, Ur, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, st));
@@ -290,6 +310,6 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
     return conv ? TN_OK : TN_ENOCONV;
 }
 
-int tsvd_columns(int m, int k) { return std::min(m, std::min(SMALL_MAX, k + std::max(8, k / 4))); }
+int tsvd_columns(int m, int k) { return std::min(m, std::min(SMALL_MAX, k + std::max(16, (3 * k) / 4))); }
 
 }  // namespace tn

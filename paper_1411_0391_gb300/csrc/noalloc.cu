@@ -7,7 +7,7 @@
 // not allowed to own device allocations and has no context workspace to lend.
 // This entry point takes only the caller's input and output buffers; its
 // scratch is the file-scope device array below, of a fixed, modest size
-// (TN_NOALLOC_SCRATCH_DOUBLES doubles, 4 MiB), which every GPU that loads the
+// (TN_NOALLOC_SCRATCH_DOUBLES doubles, 8 MiB), which every GPU that loads the
 // library holds until the process exits.
 //
 // It runs the same implementation as tn_truncated_svd (one-sided Jacobi for
@@ -19,7 +19,7 @@
 #include "kernels.cuh"
 #include "smallla.cuh"
 
-#define TN_NOALLOC_SCRATCH_DOUBLES (1 << 19)
+#define TN_NOALLOC_SCRATCH_DOUBLES (1 << 20)
 
 // Shared by every call on a device; nothing in it is assumed to start at zero
 // (each call writes every scratch entry before reading it).
@@ -50,15 +50,16 @@ int scratch_address(double** out)
 }
 
 // Doubles of scratch the call (m, k) needs: the carving of truncated_svd
-// (panels, Ritz blocks, kk x kk blocks and the Cholesky blocks of the
-// orthonormalisation).  Split-K partial sums are optional: when they do not
-// fit, the products run without splitting.
+// (panels, Ritz blocks, the kk x kk blocks B, Ub, Vb) plus the largest
+// temporary inside an iteration (the six kk x kk blocks of the refined Ritz
+// SVD; the orthonormalisations take two).  Split-K partial sums are optional:
+// when they do not fit, the products run without splitting.
 size_t need(int m, int k)
 {
     auto al = [](size_t n) { return tn_align256(n * sizeof(double)) / sizeof(double); };
     if (m <= SMALL_MAX) return al((size_t)m * m) * 2 + al(m);
     const int kk = tsvd_columns(m, k);
-    return 4 * al((size_t)m * kk) + 2 * al((size_t)m * k) + 5 * al((size_t)kk * kk) + 2 * al(kk);
+    return 4 * al((size_t)m * kk) + 2 * al((size_t)m * k) + 9 * al((size_t)kk * kk) + 2 * al(kk);
 }
 
 }  // namespace

@@ -1237,7 +1237,7 @@ int measure(Ctx& c, tn_observables* obs)
     double* top = c.ar.take((size_t)chi * chi * L);
     double* bot = c.ar.take((size_t)chi * chi * L);
     double* R1 = c.ar.take((size_t)chi * chi * L * L);
-    double* R2 = c.ar.take((size_t)chi * chi * L * L * L);
+    double* R2 = c.ar.take((size_t)chi * chi * L * L);
     double* R3 = c.ar.take((size_t)L * L * L * L);
     double* K1 = c.ar.take((size_t)2 * D * D * D * D);
     double* Ar = c.ar.take((size_t)2 * D * D * D * D);
@@ -1258,9 +1258,11 @@ int measure(Ctx& c, tn_observables* obs)
         TN_TRY(contract(c.st, c.ar, "ibm,bc->icm", dt(t1, {chi, chi, L}), Cm(e, 1), dt(top, {chi, chi, L})));
         TN_TRY(contract(c.st, c.ar, "de,efx->dfx", Cm(e, 2), Tm(e, 2), dt(t1, {chi, chi, L})));
         TN_TRY(contract(c.st, c.ar, "dfx,fj->djx", dt(t1, {chi, chi, L}), Cm(e, 3), dt(bot, {chi, chi, L})));
+        // R3[(U u), (R r), (D d), (L l)] = top.T2 (R1) against bot.T4 (R2): the two halves
+        // meet over (i, d), so no chi^2 L^3 intermediate is formed
         TN_TRY(contract(c.st, c.ar, "icm,cdn->imdn", dt(top, {chi, chi, L}), Tm(e, 1), dt(R1, {chi, L, chi, L})));
-        TN_TRY(contract(c.st, c.ar, "imdn,djx->imnjx", dt(R1, {chi, L, chi, L}), dt(bot, {chi, chi, L}), dt(R2, {chi, L, L, chi, L})));
-        TN_TRY(contract(c.st, c.ar, "imnjx,jil->mnxl", dt(R2, {chi, L, L, chi, L}), Tm(e, 3), dt(R3, {L, L, L, L})));
+        TN_TRY(contract(c.st, c.ar, "djx,jil->dxil", dt(bot, {chi, chi, L}), Tm(e, 3), dt(R2, {chi, L, chi, L})));
+        TN_TRY(contract(c.st, c.ar, "imdn,dxil->mnxl", dt(R1, {chi, L, chi, L}), dt(R2, {chi, L, chi, L}), dt(R3, {L, L, L, L})));
         TN_TRY(contract(c.st, c.ar, "UuRrDdLl,sLRDU->urdls", dt(R3, {D, D, D, D, D, D, D, D}), dt(c.A[t], {2, D, D, D, D}),
                         dt(K1, {D, D, D, D, 2})));
         TN_TRY(contract(c.st, c.ar, "urdls,tlrdu->st", dt(K1, {D, D, D, D, 2}), dt(c.A[t], {2, D, D, D, D}), dt(rho1 + 4 * t, {2, 2})));

@@ -1,0 +1,88 @@
+"""Precision form: CTMRG contractions on the tensor cores (TF32 x3 / BF16 x3) against the FP64 oracle.
+
+The products of the environment computation run in split precision, the small
+factorisations, the full-update solve, gauge fixing and the observables in
+FP64.  The bar is 1e-6 relative on the energy for TF32 x3 (its products carry
+~1e-7 relative error); BF16 x3 (~4e-6 per product) is held to 1e-4 and its
+actual error is recorded by the bench.
+"""
+import numpy as np
+import pytest
+
+from oracle import ctmrg as OC
+from oracle import recycle as OR
+from paper_1411_0391_gb300 import _lib as L
+from paper_1411_0391_gb300 import build as B
+from paper_1411_0391_gb300.inputs import random_peps
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CELL = OC.checkerboard()
+E_TOL = {L.TN_TF32X3: 1e-6, L.TN_BF16X3: 1e-4}
+# normalised corner spectra: ~25x the product error (measured 3e-6 TF32 x3, 7e-5 BF16 x3)
+SPEC_TOL = {L.TN_TF32X3: 2e-5, L.TN_BF16X3: 5e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    L.lib()
+
+
+@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3])
+def test_converged_spectra_precision(prec):
+    D, chi = 2, 12
+    A = random_peps(2, D, instance=3)
+    ctx = L.Context(D, chi, precision=prec)
+    ctx.tn_set_state(A)
+    ctx.tn_build_double_layer()
+    ctx.tn_reset_env()
+    ctx.tn_ctmrg(1e-7, 300)
+    sp = ctx.tn_corner_spectra()
+    st, it, d, conv = OC.ctmrg(CELL, [OC.double_layer(x) for x in A], chi, 1e-11, 300)
+    ref = OC.corner_spectra(st)
+    for i, (x, y) in enumerate([(0, 0), (1, 0), (0, 1), (1, 1)]):
+        for c in range(4):
+            np.testing.assert_allclose(sp[i, c], ref[(x, y, 'C%d' % (c + 1))], atol=SPEC_TOL[prec])
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3])
+def test_trajectory_energy_precision(prec):
+    """Five plain full-update steps (h = 3, tau = 0.01, D = 2, chi = 8): energy vs the FP64 oracle."""
+    D, chi, h, tau, inst = 2, 8, 3.0, 0.01, 8
+    A = random_peps(2, D, instance=inst)
+    ctx = L.Context(D, chi, precision=prec)
+    ctx.tn_set_hamiltonian(1.0, h)
+    ctx.tn_set_time_step(tau)
+    ctx.tn_set_state(A)
+    cfg = OR.Config(h=h, tau=tau, D=D, chi=chi, ctm_tol=1e-10, ctm_max=500)
+    env, Ao = None, A
+    for _ in range(5):
+        ctx.tn_fu_step(1e-8, 500)
+        Ao, env, info = OR.fu_step(Ao, CELL, cfg, env)
+    ctx.tn_build_double_layer()
+    ctx.tn_reset_env()
+    ctx.tn_ctmrg(1e-8, 500)
+    g = ctx.tn_measure()
+    o = OR.energy(Ao, CELL, cfg, tol=1e-12)
+    err = abs(g['e_site'] - o['e_site']) / abs(o['e_site'])
+    assert err < E_TOL[prec], err
+    ctx.close()
+
+
+def test_full_size_iteration_precision_vs_f64():
+    """One CTMRG iteration at D = 4, chi = 64: TF32 x3 spectra against the FP64 GPU form."""
+    D, chi = 4, 64
+    A = random_peps(2, D, instance=4)
+    out = {}
+    for prec in (L.TN_F64, L.TN_TF32X3):
+        ctx = L.Context(D, chi, precision=prec)
+        ctx.tn_set_state(A)
+        ctx.tn_build_double_layer()
+        ctx.tn_reset_env()
+        ctx.tn_ctmrg_moves(4)
+        out[prec] = ctx.tn_corner_spectra()
+        ctx.close()
+    assert np.max(np.abs(out[L.TN_TF32X3] - out[L.TN_F64])) < SPEC_TOL[L.TN_TF32X3]
