@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--profile-moves", type=int, default=0,
                    help="run only this many CTMRG moves and one update at the workload shape (for ncu)")
     p.add_argument("--profile-precision", default="tf32x3", choices=sorted(PRECISIONS))
+    p.add_argument("--profile-gemm", action="store_true",
+                   help="run only the N x N x N products of the workload (tcgen05 TF32x3 and FP64), 3 launches each")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -313,17 +315,37 @@ def run_gpu(args):
     D, chi = WL["D"], WL["chi"]
     state = random_peps(2, D, instance=rank)          # replicas: independent instances per rank
 
+    if args.profile_gemm:
+        N = chi * D * D
+        A = torch.randn(N, N, dtype=torch.float64, device=dev)
+        B = torch.randn(N, N, dtype=torch.float64, device=dev)
+        C = torch.empty(N, N, dtype=torch.float64, device=dev)
+        work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_TF32X3, N, N, N), dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            L.tn_gemm_split(L.TN_TF32X3, 0, 0, N, N, N, 1.0, A, N, B, N, 0.0, C, N, work, stream)
+        for _ in range(3):
+            L.tn_gemm_f64(0, 0, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, 0, 1, stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_gemm": N, "launches": L.tn_launch_count()}))
+        return
+
     if args.profile_moves:
+        # steady state: a developed environment (8 iterations, past the FP64 start of the
+        # split forms), then the profiled moves and one update; "skip" = launches before them
         ctx = L.Context(D, chi, device=dev, precision=PRECISIONS[args.profile_precision])
         ctx.tn_set_hamiltonian(1.0, WL["h"])
         ctx.tn_set_time_step(WL["tau"])
         ctx.tn_set_state(state)
         ctx.tn_step_prepare()
+        ctx.tn_ctmrg(0.0, 8)
+        torch.cuda.synchronize()
+        skip = L.tn_launch_count()
+        ctx.tn_step_prepare()
         ctx.tn_ctmrg_moves(args.profile_moves)
         ctx.tn_step_update()
         torch.cuda.synchronize()
         print(json.dumps({"profile_moves": args.profile_moves, "precision": args.profile_precision,
-                          "launches": L.tn_launch_count()}))
+                          "skip": skip, "launches": L.tn_launch_count() - skip}))
         return
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)       # larger than the 129 MB L2

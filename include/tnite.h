@@ -60,12 +60,16 @@ typedef struct tn_config {
     int D;          /* PEPS bond dimension, 1..8 */
     int chi;        /* CTM bond dimension, 1 <= chi <= 96 */
     int cell;       /* TN_CELL_CHECKERBOARD or TN_CELL_SINGLE */
-    int precision;  /* arithmetic of the CTMRG contractions (enlarged corners,
-                       half-system products, products of the projector SVD,
-                       renormalisation): TN_F64, TN_TF32X3 or TN_BF16X3.  The
-                       small factorisations, the bond environment, the
-                       full-update solve, gauge fixing and observables are
-                       FP64 in every mode. */
+    int precision;  /* arithmetic of the CTMRG contractions (C.T, enlarged
+                       corners, half-system and loop products, projector
+                       products, renormalisation): TN_F64, TN_TF32X3 or
+                       TN_BF16X3.  The split forms start in FP64 after
+                       tn_reset_env and switch once the environment has
+                       developed (corner spectra within 1e-4 between
+                       iterations, or 32 moves); an environment given by
+                       tn_set_env counts as developed.  The projector SVD,
+                       bond environment, full-update solve, gauge fixing and
+                       observables are FP64 in every mode. */
 } tn_config;
 
 /* Number of kernels this library has launched in the process so far (all
@@ -157,6 +161,13 @@ int tn_step_update(void* ctx, tn_step_report* rep);
 /* Plain full-update step: prepare, CTMRG(ctm_tol, ctm_max), update. */
 int tn_fu_step(void* ctx, double ctm_tol, int ctm_max, tn_step_report* rep);
 
+/* One simple-update step (no environment): canonical form, Theta = gA, and
+ * every leg truncated kappa*D -> D by the lambda-weighted simple-update
+ * projectors (Sec. VI.B, last paragraph; the method Sec. VI.D compares the
+ * full update with).  The state is replaced and max-abs normalised; the
+ * environment is left as it was.  rep (optional): canon_iters. */
+int tn_su_step(void* ctx, tn_step_report* rep);
+
 /* Recycling window of Sec. VI.C: after tn_step_prepare + tn_ctmrg +
  * tn_step_update, build the renormalised gate (canonical form of A~ (a11),
  * gauge fix against A_0 (a12), leg matrices K (a13)); the state is reset to
@@ -217,6 +228,12 @@ int tn_measure(void* ctx, tn_observables* obs);
  * order (A,h), (B,h), (A,v), (B,v); (A,h), (A,v) for the 1-site cell) or
  * tensor*4 + leg.  n must equal the tensor's size (see list above). */
 int tn_get_tensor(void* ctx, int which, int index, double* host, size_t n);
+
+/* Projector cutoff (the reading of the cited CTMRG, Sec. VI.B): singular
+ * values of the loop matrix below cut * s_1 get a zero inverse square root
+ * (the direction is dropped).  Default 1e-12; cut < 0 restores the default.
+ * TN_EINVAL for NaN. */
+int tn_set_projector_cutoff(void* ctx, double cut);
 
 /* ---- kernel-level entry points (device pointers, used by the parity tests
  *      and usable on their own) ----------------------------------------- */

@@ -1,5 +1,8 @@
 """Imaginary-time evolution with full update and environment recycling (oracle), Sec. VI.B-C.
 
+Simple-update step (su_step, the comparison method of Sec. VI.D): rows a11,
+a1, a7 and the pre-truncated sites, without environment.
+
 Plain step (every row a1-a10):
     A_c   = weighted canonical form of A, with weights lambda           (a11)
     Theta = g A_c                                                        (a1)
@@ -59,6 +62,20 @@ def fu_step(A, cell, cfg, env=None, g=None):
     info = dict(A0=Ac, lam=can['lam'], Theta=Theta, pre=pre, fu=fu, ctm_iters=it,
                 ctm_delta=delta, ctm_converged=conv, als=als_info, state=st)
     return At, st.env, info
+
+
+def su_step(A, cell, cfg, g=None):
+    """One simple-update step: the environment-free method of the comparison in Sec. VI.D.
+
+    Canonical form (weights lambda), Theta = g A_c, and every leg truncated by
+    the lambda-weighted simple-update projectors of the pre-truncation (a7);
+    the result is max-abs normalised.
+    """
+    g = ipepo(cfg.h, cfg.tau) if g is None else g
+    can = canonicalize(A, cell, cfg.canon_tol, cfg.canon_max)
+    Theta = [apply_pepo(g, a) for a in can['A']]
+    pre = pretruncation(Theta, cell, can['lam'], cfg.D)
+    return [x / np.abs(x).max() for x in pretruncated_sites(Theta, cell, pre)]
 
 
 def gate_legs(cell, fu, maps, W):

@@ -74,12 +74,14 @@ _SIGS = {
     "tn_step_prepare": (c_int, [c_void_p, POINTER(tn_step_report)]),
     "tn_step_update": (c_int, [c_void_p, POINTER(tn_step_report)]),
     "tn_fu_step": (c_int, [c_void_p, c_double, c_int, POINTER(tn_step_report)]),
+    "tn_su_step": (c_int, [c_void_p, POINTER(tn_step_report)]),
     "tn_recycle": (c_int, [c_void_p, c_int, _DP]),
     "tn_evolve": (c_int, [c_void_p, c_int, POINTER(tn_evolve_opts), POINTER(tn_evolve_report)]),
     "tn_measure": (c_int, [c_void_p, POINTER(tn_observables)]),
     "tn_get_tensor": (c_int, [c_void_p, c_int, c_int, _DP, c_size_t]),
     "tn_gemm_f64": (c_int, [c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_longlong,
                             c_void_p, c_int, c_longlong, c_double, c_void_p, c_int, c_longlong, c_int, c_void_p]),
+    "tn_set_projector_cutoff": (c_int, [c_void_p, c_double]),
     "tn_gemm_split_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int]),
     "tn_gemm_split": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
                               c_double, c_void_p, c_int, c_void_p, c_size_t, c_void_p]),
@@ -306,6 +308,11 @@ class Context:
         _check(lib().tn_fu_step(self.handle, ctm_tol, ctm_max, byref(rep)), "tn_fu_step", allow_noconv=True)
         return self._step(rep)
 
+    def tn_su_step(self):
+        r = tn_step_report()
+        _check(lib().tn_su_step(self.handle, byref(r)), "tn_su_step")
+        return dict(canon_iters=r.canon_iters)
+
     def tn_recycle(self, n_re):
         F = c_double(0.0)
         _check(lib().tn_recycle(self.handle, n_re, byref(F)), "tn_recycle")
@@ -317,6 +324,9 @@ class Context:
         _check(lib().tn_evolve(self.handle, n_steps, byref(o), byref(rep)), "tn_evolve")
         return dict(steps=rep.steps, env_computations=rep.env_computations, ctm_iterations=rep.ctm_iterations,
                     ctm_moves=rep.ctm_moves, nonconverged=rep.nonconverged, last_fidelity=rep.last_fidelity)
+
+    def tn_set_projector_cutoff(self, cut):
+        _check(lib().tn_set_projector_cutoff(self.handle, cut), "tn_set_projector_cutoff")
 
     def tn_measure(self):
         o = tn_observables()

@@ -294,6 +294,7 @@ int tn_set_env(void* ctx, const double* host, size_t n)
     TN_CUDA(cudaMemcpyAsync(c.envbuf, host, n * sizeof(double), cudaMemcpyHostToDevice, c.st));
     TN_CUDA(cudaStreamSynchronize(c.st));
     c.prev_spectra.clear();
+    c.split_ready = true;           // a supplied environment counts as developed
     return TN_OK;
 }
 
@@ -358,6 +359,16 @@ int tn_fu_step(void* ctx, double ctm_tol, int ctm_max, tn_step_report* rep)
     TN_TRY(tn_step_update(ctx, &r));
     if (rep) *rep = r;
     return s;
+}
+
+int tn_su_step(void* ctx, tn_step_report* rep)
+{
+    if (!ctx) return TN_EINVAL;
+    tn_step_report r{};
+    TN_TRY(su_step(*C(ctx), &r));
+    TN_CUDA(cudaStreamSynchronize(C(ctx)->st));
+    if (rep) *rep = r;
+    return TN_OK;
 }
 
 int tn_recycle(void* ctx, int n_re, double* fidelity)
@@ -446,6 +457,13 @@ int tn_gemm_f64(int transA, int transB, int m, int n, int k, double alpha,
     if (m < 0 || n < 0 || k < 0 || batch < 0 || (m * n > 0 && (!dA || !dB || !dC))) return TN_EINVAL;
     return gemm(reinterpret_cast<cudaStream_t>(stream), transA != 0, transB != 0, m, n, k, alpha,
                 dA, lda, strideA, dB, ldb, strideB, beta, dC, ldc, strideC, batch);
+}
+
+int tn_set_projector_cutoff(void* ctx, double cut)
+{
+    if (!ctx || cut != cut) return TN_EINVAL;
+    static_cast<Ctx*>(ctx)->cut_override = cut < 0.0 ? -1.0 : cut;
+    return TN_OK;
 }
 
 size_t tn_gemm_split_workspace_bytes(int precision, int m, int n, int k)

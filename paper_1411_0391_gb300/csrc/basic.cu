@@ -362,11 +362,7 @@ __global__ void hash_fill_kernel(double* x, long long n, unsigned long long seed
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z = z ^ (z >> 31);
-        x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+        x[i] = tn_hash_uniform(seed, i);
     }
 }
 

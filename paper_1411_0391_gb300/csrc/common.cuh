@@ -18,6 +18,16 @@ void tn_count_launch();
 // after every kernel launch: count it and surface launch errors
 #define TN_LAUNCHED() do { tn_count_launch(); TN_CUDA(cudaGetLastError()); } while (0)
 
+// Counter-based uniform number in [-1, 1): splitmix64 of (seed, index).
+__host__ __device__ inline double tn_hash_uniform(unsigned long long seed, long long i)
+{
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
 static inline size_t tn_align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Bump allocator over a caller-owned device buffer.  mark()/release() give

@@ -86,6 +86,8 @@ int ctx_reset_env(Ctx& c)
     TN_LAUNCHED();
     for (int r = 0; r < 4; ++r) for (int x = 0; x < 4; ++x) for (int y = 0; y < 4; ++y) c.warm_ok[r][x][y] = false;
     c.prev_spectra.clear();
+    c.split_ready = false;
+    c.fp64_moves = 0;
     return TN_OK;
 }
 
@@ -242,6 +244,7 @@ int ctmrg_move(Ctx& c, Frame& f)
         (void)N;
     }
     ++c.ctm_moves;
+    if (!c.split_ready && ++c.fp64_moves >= 32) c.split_ready = true;
     return TN_OK;
 }
 
@@ -302,6 +305,7 @@ int ctmrg_iterations(Ctx& c, double tol, int max_iter, tn_ctm_report* rep)
             delta = std::max(delta, std::sqrt(acc));
         }
         c.prev_spectra = cur;
+        if (delta <= 1e-4) c.split_ready = true;
         if (!std::isfinite(delta)) {
             if (rep) { rep->iterations = it; rep->converged = 0; rep->delta = delta; rep->svd_calls = 0; rep->svd_iterations = 0; }
             return TN_ENUMERIC;

@@ -62,6 +62,15 @@ struct Ctx {
     Env env0[MAXS];            // environment storage in the unrotated frame
     double* warmV[4][4][4];    // projector right vectors (rotation, x, y) for warm starts
     bool warm_ok[4][4][4];
+    double cut_override = -1.0;   // projector cutoff set by tn_set_projector_cutoff (< 0: default)
+    // Precision schedule of the split forms: after an environment reset the
+    // moves run in FP64 until the environment has developed (corner spectra
+    // within 1e-4 of the previous iteration, or 32 moves); only then the
+    // contractions switch to the tensor cores.  From the low-rank start the
+    // loop matrix has many directions at the product-error level, which
+    // S^{-1/2} amplifies into a wrong fixed point.
+    bool split_ready = false;
+    int fp64_moves = 0;
     double* Pup[4];            // projectors of the current column, per y
     double* Plo[4];
     double* dscratch = nullptr;   // small device scratch (reports)
@@ -72,18 +81,20 @@ struct Ctx {
     std::vector<double> prev_spectra;
 
     int N() const { return chi * leg; }
-    // contraction arithmetic of the CTMRG moves: -1 FP64, 0 TF32 x3, 1 BF16 x3
-    int kind() const { return cfg.precision == TN_TF32X3 ? 0 : cfg.precision == TN_BF16X3 ? 1 : -1; }
+    // contraction arithmetic of the CTMRG moves now: -1 FP64, 0 TF32 x3, 1 BF16 x3
+    int kind() const
+    {
+        if (!split_ready) return -1;
+        return cfg.precision == TN_TF32X3 ? 0 : cfg.precision == TN_BF16X3 ? 1 : -1;
+    }
     // Ritz residual threshold (relative to s_1) of the FP64 projector SVD: the loop
     // matrix of the precision form is itself known only to the accuracy of its
     // split products (~1e-7 TF32 x3, ~4e-6 BF16 x3), so resolving it further
     // than 1e-10 (1e-9) buys nothing
-    double svd_tol() const { return cfg.precision == TN_TF32X3 ? 1e-10 : cfg.precision == TN_BF16X3 ? 1e-9 : 1e-13; }
+    double svd_tol() const { return kind() == 0 ? 1e-10 : kind() == 1 ? 1e-9 : 1e-13; }
     // inverse-square-root cutoff of the projectors (relative to s_1): singular
-    // values of the loop matrix below it are dropped.  1e-12 in FP64; in the
-    // precision form the loop matrix is known only to its product error, and
-    // directions below ~8x that error are noise that S^{-1/2} would amplify
-    double proj_cut() const { return cfg.precision == TN_TF32X3 ? 1e-6 : cfg.precision == TN_BF16X3 ? 3e-5 : 1e-12; }
+    // values of the loop matrix below it are dropped (1e-12 unless overridden)
+    double proj_cut() const { return cut_override >= 0.0 ? cut_override : 1e-12; }
     size_t env_size() const { return (size_t)nsites * (4 * (size_t)chi * chi + 4 * (size_t)chi * chi * leg); }
     Frame frame0();
 };
@@ -103,6 +114,7 @@ int build_double_layers(Ctx& c, double* const* sites, int Dsite);
 int canonicalize(Ctx& c, double* const* A, double* const* Aout, int* iters, bool keep_maps);
 int step_prepare(Ctx& c, tn_step_report* rep);
 int step_update(Ctx& c, tn_step_report* rep);
+int su_step(Ctx& c, tn_step_report* rep);
 int recycle(Ctx& c, int n_re, double* F);
 int measure(Ctx& c, tn_observables* obs);
 

@@ -259,9 +259,11 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
     double* Sb = ar.take(kk);
     double* rn = ar.take(kk);
     if (!Om || !Y || !Z || !T || !TV || !Ur || !B || !Ub || !Vb || !Sb || !rn) { ar.release(mk); return TN_ENOMEM; }
+    // start: the warm right vectors (k columns) and fresh random oversampling columns
     TN_TRY(hash_fill(st, Om, (long long)m * kk, 0x5eed0000ull + (unsigned long long)m * 131 + k));
     if (warm)
-        TN_CUDA(cudaMemcpy2DAsync(Om, kk * sizeof(double), warm, k * sizeof(double), k * sizeof(double), m, cudaMemcpyDeviceToDevice, st));
+        TN_CUDA(cudaMemcpy2DAsync(Om, kk * sizeof(double), warm, k * sizeof(double), k * sizeof(double), m,
+                                  cudaMemcpyDeviceToDevice, st));
     double hs[SMALL_MAX], hr[SMALL_MAX];
     const int max_it = 16;
     int it = 0;
@@ -272,13 +274,15 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
         const bool first = (it == 1);
         if (kind >= 0) TN_TRY(gemm_tc(st, ar, kind, false, false, m, kk, m, 1.0, M, m, Om, kk, 0.0, Y, kk));
         else TN_TRY(gemm_splitk(st, ar, false, false, m, kk, m, 1.0, M, m, Om, kk, 0.0, Y, kk));
-        // the first basis (random or warm) may be ill conditioned: FP64 shifted CholeskyQR3;
-        // afterwards the panels are near orthogonal and FP32 whitening + FP64 fixes suffice
-        if (first) TN_TRY(orth2(st, ar, Y, T, m, kk, true));
+        // the first basis (random or warm + random) may be ill conditioned: FP64 shifted
+        // CholeskyQR3; afterwards the panels are near orthogonal and FP32 whitening +
+        // FP64 fixes suffice
+        const bool fp64_orth = first;
+        if (fp64_orth) TN_TRY(orth2(st, ar, Y, T, m, kk, true));
         else TN_TRY(orth_mixed(st, ar, Y, T, m, kk, 2));
         if (kind >= 0) TN_TRY(gemm_tc(st, ar, kind, true, false, m, kk, m, 1.0, M, m, Y, kk, 0.0, Z, kk));
         else TN_TRY(gemm_splitk(st, ar, true, false, m, kk, m, 1.0, M, m, Y, kk, 0.0, Z, kk));
-        if (first) TN_TRY(orth2(st, ar, Z, T, m, kk, true));
+        if (fp64_orth) TN_TRY(orth2(st, ar, Z, T, m, kk, true));
         else TN_TRY(orth_mixed(st, ar, Z, T, m, kk, 2));
         if (kind >= 0) TN_TRY(gemm_tc(st, ar, kind, false, false, m, kk, m, 1.0, M, m, Z, kk, 0.0, T, kk));
         else TN_TRY(gemm_splitk(st, ar, false, false, m, kk, m, 1.0, M, m, Z, kk, 0.0, T, kk));

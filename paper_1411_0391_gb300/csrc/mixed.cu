@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) chol32_whiten_kernel(const double* __rest
 {
     extern __shared__ float fs[];
     float* R = fs;                 // n*n, row j = row j of R after the factorisation
-    float* Ri = R + n * n;         // n*n, R^{-1}
+    float* Ri = R + n * n;         // n*n, R^{-1}; then n*n of scratch
     __shared__ double dsc[SMALL_MAX];
     __shared__ int dead[SMALL_MAX];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -76,17 +76,34 @@ __global__ void __launch_bounds__(256) chol32_whiten_kernel(const double* __rest
         }
         __syncthreads();
     }
-    // R^{-1} by back substitution, one column per thread
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        for (int i = 0; i < n; ++i) Ri[i * n + c] = 0.0f;
-        Ri[c * n + c] = 1.0f / R[c * n + c];
-        for (int i = c - 1; i >= 0; --i) {
-            float acc = 0.0f;
-            for (int l = i + 1; l <= c; ++l) acc = fmaf(R[i * n + l], Ri[l * n + c], acc);
-            Ri[i * n + c] = -acc / R[i * n + i];
-        }
+    // R^{-1} by doubling over diagonal blocks: with the inverses X_AA, X_CC of two
+    // adjacent b x b diagonal blocks known, X_AC = -X_AA R_AC X_CC; every pair of a
+    // level is independent, so a level is two parallel products (log2 n levels)
+    float* Tm = Ri + n * n;        // n*n scratch: R_AC X_CC
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        Ri[e] = (i == j) ? 1.0f / R[e] : 0.0f;
     }
     __syncthreads();
+    for (int b = 1; b < n; b *= 2) {
+        // element (i, j) of a pair: i in A = [k, k+b), j in C = [k+b, k+2b), k a multiple of 2b
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = e / n, j = e % n, k = (i / (2 * b)) * (2 * b);
+            if (i >= k + b || j < k + b || j >= k + 2 * b) continue;
+            float acc = 0.0f;
+            for (int l = k + b; l <= j; ++l) acc = fmaf(R[i * n + l], Ri[l * n + j], acc);
+            Tm[e] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = e / n, j = e % n, k = (i / (2 * b)) * (2 * b);
+            if (i >= k + b || j < k + b || j >= k + 2 * b) continue;
+            float acc = 0.0f;
+            for (int l = i; l < k + b; ++l) acc = fmaf(Ri[i * n + l], Tm[l * n + j], acc);
+            Ri[e] = -acc;
+        }
+        __syncthreads();
+    }
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, c = e % n;
         X[e] = dead[c] ? 0.0 : dsc[i] * (double)Ri[e];
@@ -138,7 +155,7 @@ __global__ void __launch_bounds__(256) orth_fix_kernel(const double* __restrict_
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xo[e] = X[e];
 }
 
-size_t chol32_smem(int n) { return sizeof(float) * 2 * (size_t)n * n + 64; }
+size_t chol32_smem(int n) { return sizeof(float) * 3 * (size_t)n * n + 64; }
 size_t orthfix_smem(int n) { return sizeof(double) * 2 * (size_t)n * n + sizeof(int) * n + 64; }
 
 // ---------------------------------------------------------------------------
@@ -146,8 +163,16 @@ size_t orthfix_smem(int n) { return sizeof(double) * 2 * (size_t)n * n + sizeof(
 // row-major FP64, columns sorted by descending singular value; columns of
 // zero norm give zero U columns).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) svd32_kernel(const double* __restrict__ B, int n,
-                                                    double* __restrict__ U0, double* __restrict__ V0)
+__device__ __forceinline__ float half_sum_f(float v, unsigned mask)
+{
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, 16);
+    return v;
+}
+
+// One pair per half-warp (16 lanes): with 1024 threads every pair of a round
+// (n/2 <= 56) runs at once, so a round costs one pair's latency.
+__global__ void __launch_bounds__(1024) svd32_kernel(const double* __restrict__ B, int n,
+                                                     double* __restrict__ U0, double* __restrict__ V0)
 {
     extern __shared__ float fs[];
     float* A = fs;                 // column-major n x n: column j at A + j*n
@@ -177,37 +202,39 @@ __global__ void __launch_bounds__(512) svd32_kernel(const double* __restrict__ B
     __syncthreads();
     const float tol = fmaxf(1e-6f, 2.0f * n * 6e-8f);
     const int M = n + (n & 1);
+    const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15, nhw = blockDim.x >> 4;
+    const unsigned hmask = 0xffffu << (16 * ((threadIdx.x >> 4) & 1));
     for (int sweep = 0; sweep < 40; ++sweep) {
         if (threadIdx.x == 0) rotated = 0;
         __syncthreads();
         for (int r = 0; r < M - 1; ++r) {
-            for (int k = warp; k < M / 2; k += nw) {
+            for (int k = hw; k < M / 2; k += nhw) {
                 int p, q;
                 rr_pair(M, r, k, p, q);
-                if (q >= n) continue;
+                if (q >= n) continue;              // uniform over the half-warp
                 float* ap = A + p * n;
                 float* aq = A + q * n;
                 float al = 0.0f, be = 0.0f, ga = 0.0f;
-                for (int i = lane; i < n; i += 32) {
+                for (int i = hl; i < n; i += 16) {
                     const float x = ap[i], y = aq[i];
                     al = fmaf(x, x, al); be = fmaf(y, y, be); ga = fmaf(x, y, ga);
                 }
-                al = warp_sum_f(al); be = warp_sum_f(be); ga = warp_sum_f(ga);
+                al = half_sum_f(al, hmask); be = half_sum_f(be, hmask); ga = half_sum_f(ga, hmask);
                 if (ga == 0.0f || fabsf(ga) <= tol * sqrtf(al * be) || al < 1e-30f || be < 1e-30f) continue;
                 const float zeta = (be - al) / (2.0f * ga);
                 const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
                 const float c = rsqrtf(1.0f + t * t), s = c * t;
-                for (int i = lane; i < n; i += 32) {
+                for (int i = hl; i < n; i += 16) {
                     const float x = ap[i], y = aq[i];
                     ap[i] = c * x - s * y; aq[i] = s * x + c * y;
                 }
                 float* vp = V + p * n;
                 float* vq = V + q * n;
-                for (int i = lane; i < n; i += 32) {
+                for (int i = hl; i < n; i += 16) {
                     const float x = vp[i], y = vq[i];
                     vp[i] = c * x - s * y; vq[i] = s * x + c * y;
                 }
-                if (lane == 0) rotated = 1;
+                if (hl == 0) rotated = 1;
             }
             __syncthreads();
         }
@@ -323,7 +350,7 @@ int svd_mixed(cudaStream_t st, Arena& ar, const double* B, int n, double* U, dou
     double* F = ar.take(nn);
     double* G = ar.take(nn);
     if (!Rm || !Sm || !BV || !T || !F || !G) { ar.release(mk); return TN_ENOMEM; }
-    svd32_kernel<<<1, 512, svd32_smem(n), st>>>(B, n, U, V);
+    svd32_kernel<<<1, 1024, svd32_smem(n), st>>>(B, n, U, V);
     TN_LAUNCHED();
     for (int it = 0; it < steps; ++it) {
         TN_TRY(gemm(st, true, false, n, n, n, 1.0, U, n, 0, U, n, 0, 0.0, Rm, n, 0, 1));

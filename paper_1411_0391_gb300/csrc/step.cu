@@ -978,7 +978,8 @@ static int apply_legs(Ctx& c, const double* T, double* out, int t, double* const
     return TN_OK;
 }
 
-int step_prepare(Ctx& c, tn_step_report* rep)
+// Canonical form, Theta = g A_c and the simple-update projectors (a11, a1, a7).
+static int prepare_theta(Ctx& c, int* canon_iters)
 {
     if (!c.have_state) return TN_ESTATE;
     if (!c.have_pepo) return TN_ESTATE;
@@ -994,6 +995,14 @@ int step_prepare(Ctx& c, tn_step_report* rep)
     size_t smem = sizeof(double) * (10 * (size_t)n2 + 3 * n + 2 * (n / 2 + 1)) + sizeof(int) * 2 * (n / 2 + 1) + 64;
     pretrunc_kernel<<<c.nl, 256, smem, c.st>>>(pa);
     TN_LAUNCHED();
+    *canon_iters = it;
+    return TN_OK;
+}
+
+int step_prepare(Ctx& c, tn_step_report* rep)
+{
+    int it = 0;
+    TN_TRY(prepare_theta(c, &it));
     for (int t = 0; t < c.nt; ++t) TN_TRY(apply_legs(c, c.Theta[t], c.A1[t], t, c.preP, c.preQ, c.kD));   // A'
     if (c.leg != c.D * c.D) return TN_ESTATE;
     TN_TRY(build_double_layers(c, c.A1, c.D));                          // a2
@@ -1095,6 +1104,23 @@ static int bond_env(Ctx& c, int e, double* out)
     TN_TRY(contract(c.st, c.ar, "onAa,onBb->AaBb", dt(EL, {chi, chi, k, k}), dt(ER, {chi, chi, k, k}), dt(Nr, {k, k, k, k})));
     TN_TRY(permute_spec(c.st, "AaBb->ABab", dt(Nr, {k, k, k, k}), dt(out, {k, k, k, k})));
     c.ar.release(mk);
+    return TN_OK;
+}
+
+// Simple-update step (the environment-free method the full update is compared
+// with, Sec. VI.B last paragraph and Sec. VI.D): A <- Theta truncated on every
+// leg by the lambda-weighted projectors of a7, max-abs normalised.
+int su_step(Ctx& c, tn_step_report* rep)
+{
+    int it = 0;
+    TN_TRY(prepare_theta(c, &it));
+    for (int t = 0; t < c.nt; ++t) {
+        TN_TRY(apply_legs(c, c.Theta[t], c.A[t], t, c.preP, c.preQ, c.kD));
+        TN_TRY(normalize_maxabs(c.st, c.A[t], 2LL * c.D * c.D * c.D * c.D, 1, 0));
+    }
+    c.prepared = false;
+    c.updated = false;
+    if (rep) rep->canon_iters = it;
     return TN_OK;
 }
 

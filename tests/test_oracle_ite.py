@@ -71,3 +71,53 @@ def test_large_field_against_exact_diagonalisation():
     m = R.energy(A, cell, cfg)
     assert abs(m['e_site'] - e_ed) < 3e-3
     assert m['e_site'] > e_ed - 1e-4          # a variational state cannot go below the ground state by more than finite-size effects
+
+
+# --- simple-update step (the comparison method of Sec. VI.D) ---------------------------------
+
+def test_su_d1_reaches_mean_field():
+    """At D = 1 the simple update is mean-field imaginary-time evolution: E_site -> -2 - h^2/8,
+    with the second-order Trotter error O(tau^2) (the error quarters when tau halves)."""
+    h = 2.0
+    cell = C.checkerboard()
+    A = random_peps(2, 1, instance=6)
+    cfg = R.Config(h=h, tau=0.05, D=1, chi=2)
+    for _ in range(100):
+        A = R.su_step(A, cell, cfg)
+    err = {}
+    for tau, n in ((0.01, 200), (0.005, 200)):
+        cfg.tau = tau
+        for _ in range(n):
+            A = R.su_step(A, cell, cfg)
+        err[tau] = R.energy(A, cell, cfg)['e_site'] - (-2.0 - h * h / 8.0)
+    assert 0.0 < err[0.005] < 1e-4
+    assert 3.2 < err[0.01] / err[0.005] < 4.8
+
+
+def test_su_h0_product_state_is_fixed_point():
+    cell = C.checkerboard()
+    A = np.zeros((2, 2, 2, 2, 2))
+    A[0, 0, 0, 0, 0] = 1.0
+    A = A + 1e-6 * np.random.default_rng(1).standard_normal(A.shape)
+    A = [A, A.copy()]
+    cfg = R.Config(h=0.0, tau=0.01, D=2, chi=4)
+    for _ in range(5):
+        A = R.su_step(A, cell, cfg)
+    m = R.energy(A, cell, cfg)
+    assert abs(m['e_site'] + 2.0) < 1e-10
+
+
+def test_su_above_fu_variationally():
+    """Both methods give variational states of the same ansatz; on the ordered side
+    (h = 2.5, D = 2) the simple update, which ignores the environment, ends higher."""
+    h = 2.5
+    cell = C.checkerboard()
+    A0 = random_peps(2, 2, instance=7)
+    cfg = R.Config(h=h, tau=0.05, D=2, chi=8, ctm_max=200)
+    Asu = A0
+    for _ in range(40):
+        Asu = R.su_step(Asu, cell, cfg)
+    Afu, env, _ = R.evolve(A0, cell, cfg, 40)
+    esu = R.energy(Asu, cell, cfg)['e_site']
+    efu = R.energy(Afu, cell, cfg, env=env)['e_site']
+    assert efu < esu
