@@ -357,12 +357,8 @@ def run_gpu(args):
         for name in ("tf32x3", "f64", "bf16x3"):
             ctxs[name], results[name] = time_form(L, torch, dev, stream, PRECISIONS[name], state, args, flush)
     head = results["tf32x3"]
-    total, t_ctm = head["total"], head["t_ctm"]
-    if dist:
-        t = torch.tensor([total, t_ctm], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total, t_ctm = float(t[0]), float(t[1])
-    value = world * args.steps / total
+    total, t_ctm = max_over_ranks([head["total"], head["t_ctm"]], dist, dev)
+    value = whole_job_rate(world, args.steps, total)
 
     import numpy as np
     # energy at full size.  (1) The environment's precision alone: the FP64 form's evolved state,
@@ -469,6 +465,21 @@ def workload_config(world):
                          "tensor cores, projector SVD / bond environment / ALS / gauge fix FP64" % CTM_ITERS,
                 **WL, ctm_iterations_per_step=CTM_ITERS, parallelism="replicas" if world > 1 else "single",
                 l2="flushed between timed steps (256 MB write)")
+
+
+def max_over_ranks(values, dist=None, device=None):
+    """Element-wise max over ranks of host floats (identity without a process group)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(world, units_per_rank, slowest_seconds):
+    """Units of all ranks / the slowest rank's time (replicas: every rank does the same work)."""
+    return world * units_per_rank / slowest_seconds
 
 
 def measured_peaks():

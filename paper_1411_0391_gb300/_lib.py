@@ -15,7 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _PATH = os.path.join(_HERE, "libtnite.so")
 _LIB = None
 
-TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE, TN_ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE, TN_ESCRATCH, TN_ETIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
 TN_CELL_CHECKERBOARD, TN_CELL_SINGLE = 2, 1
 TN_F64, TN_TF32X3, TN_BF16X3 = 0, 1, 2
 (TN_T_STATE, TN_T_CANON, TN_T_LAMBDA, TN_T_THETA, TN_T_PRE_P, TN_T_PRE_Q, TN_T_DOUBLE,

@@ -57,3 +57,53 @@ def test_status_strings(libpath):
     from paper_1411_0391_gb300 import _lib
     assert _lib.lib().tn_strerror(_lib.TN_EINVAL) == b"invalid argument"
     assert _lib.lib().tn_strerror(_lib.TN_ENOCONV).startswith(b"iteration cap")
+
+
+def test_precision_forms_validated_on_host(libpath):
+    """Every precision value of tn_config is accepted by the workspace query; others are not."""
+    from paper_1411_0391_gb300 import _lib
+    L = _lib.lib()
+    for prec in (_lib.TN_F64, _lib.TN_TF32X3, _lib.TN_BF16X3):
+        cfg = _lib.tn_config(2, 8, _lib.TN_CELL_CHECKERBOARD, prec)
+        assert L.tn_workspace_bytes(ctypes.byref(cfg)) > 0
+    bad = _lib.tn_config(2, 8, _lib.TN_CELL_CHECKERBOARD, 7)
+    assert L.tn_workspace_bytes(ctypes.byref(bad)) == 0
+
+
+def test_split_gemm_workspace_is_the_padded_operands(libpath):
+    """Head and tail of each operand, K-major, rows padded to the 128 x 64 tile and K to 128 bytes."""
+    from paper_1411_0391_gb300 import _lib
+    L = _lib.lib()
+    def al(x):
+        return (x + 255) // 256 * 256
+    m, n, k = 200, 150, 70
+    # TF32: 4-byte elements, K padded to 32; BF16: 2-byte elements, K padded to 64
+    tf = al(2 * 256 * 96 * 4) + al(2 * 192 * 96 * 4)
+    bf = al(2 * 256 * 128 * 2) + al(2 * 192 * 128 * 2)
+    assert L.tn_gemm_split_workspace_bytes(_lib.TN_TF32X3, m, n, k) == tf
+    assert L.tn_gemm_split_workspace_bytes(_lib.TN_BF16X3, m, n, k) == bf
+    assert L.tn_gemm_split_workspace_bytes(_lib.TN_F64, m, n, k) == 0
+    assert L.tn_gemm_split_workspace_bytes(_lib.TN_TF32X3, 0, n, k) == 0
+
+
+def test_argument_checks_before_any_device_call(libpath):
+    """Calls that fail validation return TN_EINVAL without touching the GPU."""
+    from paper_1411_0391_gb300 import _lib
+    L = _lib.lib()
+    assert L.tn_set_projector_cutoff(None, 1e-12) == _lib.TN_EINVAL
+    assert L.tn_su_step(None, None) == _lib.TN_EINVAL
+    assert L.tn_fu_step(None, 1e-8, 10, None) == _lib.TN_EINVAL
+    assert L.tn_gemm_split(5, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None, 0, None) == _lib.TN_EINVAL
+    assert L.tn_gemm_split(_lib.TN_TF32X3, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None, 0, None) \
+        == _lib.TN_EINVAL
+    assert L.tn_truncated_svd_noalloc(None, 8, 4, None, None, None, None, None) == _lib.TN_EINVAL
+    h = ctypes.c_void_p()
+    bad = _lib.tn_config(9, 8, _lib.TN_CELL_CHECKERBOARD, _lib.TN_F64)       # D out of range
+    assert L.tn_create(ctypes.byref(h), ctypes.byref(bad), None, 0, None) == _lib.TN_EINVAL
+
+
+def test_new_status_strings(libpath):
+    from paper_1411_0391_gb300 import _lib
+    L = _lib.lib()
+    assert b"tensor-core" in L.tn_strerror(_lib.TN_ETIMEOUT)
+    assert b"allocation-free" in L.tn_strerror(_lib.TN_ESCRATCH)
