@@ -175,23 +175,39 @@ int tn_su_step(void* ctx, tn_step_report* rep);
  * fidelity (optional out): the local fidelity F of Eq. (25). */
 int tn_recycle(void* ctx, int n_re, double* fidelity);
 
+#define TN_RECYCLE_OFF        0   /* plain full update every step */
+#define TN_RECYCLE_FIXED      1   /* windows of n_re steps per environment (Sec. VI.C) */
+#define TN_RECYCLE_THRESHOLD  2   /* windows that end when the bond environment drifts */
+
 typedef struct tn_evolve_opts {
-    int    recycle;        /* 0: plain full update every step; 1: recycle */
-    int    n_re;           /* steps per environment computation (recycle = 1) */
+    int    recycle;        /* TN_RECYCLE_OFF / _FIXED / _THRESHOLD */
+    int    n_re;           /* FIXED: steps per environment computation;
+                              THRESHOLD: the longest window */
     double ctm_tol;        /* CTMRG tolerance per environment computation */
     int    ctm_max;        /* CTMRG iteration cap */
+    double recycle_eps;    /* THRESHOLD: end the window once max over link types of
+                              ||N - N_0||_F / ||N_0||_F exceeds it (N_0: the bond
+                              environments of the window's environment computation,
+                              N: those of the current state after one warm CTMRG
+                              iteration, both normalised and positive as in a8) */
+    int    check_every;    /* THRESHOLD: recycled steps between checks (>= 1) */
 } tn_evolve_opts;
 
 typedef struct tn_evolve_report {
     int    steps;          /* imaginary-time steps done */
     int    env_computations;
-    int    ctm_iterations; /* total CTMRG iterations */
+    int    ctm_iterations; /* total CTMRG iterations (checks included) */
     int    ctm_moves;      /* total directional moves */
     int    nonconverged;   /* environment computations that hit ctm_max */
-    double last_fidelity;  /* F of the last recycling window (recycle = 1) */
+    double last_fidelity;  /* F of the last recycling window */
+    int    checks;         /* THRESHOLD: bond-environment checks made */
+    double last_change;    /* THRESHOLD: the last measured change */
 } tn_evolve_report;
 
-/* n_steps imaginary-time steps (Sec. VI.B-C). */
+/* n_steps imaginary-time steps (Sec. VI.B-C).  The threshold mode is the
+ * reading of "the environment recycled until the bond-environment change
+ * exceeds eps" (the paper itself uses a fixed N_Re).  TN_EINVAL for an
+ * unknown mode, n_re < 1 when recycling, check_every < 1 or a NaN eps. */
 int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* opts, tn_evolve_report* rep);
 
 /* ---- observables (Sec. VI.D; row a14) ----------------------------------- */

@@ -32,7 +32,7 @@ import numpy as np
 
 from .model import ipepo, apply_pepo
 from .ctmrg import double_layer, ctmrg, init_env
-from .fullupdate import (pretruncation, pretruncated_sites, full_update, assemble,
+from .fullupdate import (pretruncation, pretruncated_sites, full_update, assemble, bond_env, psd_project, link_list,
                          leg_links, leg_mul, LEG)
 from .canonical import canonicalize, gauge_fix, polar
 from .observables import measure
@@ -151,6 +151,72 @@ def evolve(A, cell, cfg, n_steps, n_re=1, recycle=False, env=None, log=None):
         if log is not None:
             log.append(dict(step=done, ctm_iters=info['ctm_iters'], F=info.get('F')))
     return A, env, n_env
+
+
+def bond_envs(A, cell, cfg, env, g=None, ctm_iters=1):
+    """Bond environments of the current state: canonical form, Theta, pre-truncation and
+    double layers as in a plain step, ctm_iters warm CTMRG iterations, then every N of
+    row a8 normalised by <g|g> and projected on its positive part (as the ALS sees it).
+
+    Returns (N dict by link, env after the iterations).
+    """
+    g = ipepo(cfg.h, cfg.tau) if g is None else g
+    can = canonicalize(A, cell, cfg.canon_tol, cfg.canon_max)
+    Theta = [apply_pepo(g, a) for a in can['A']]
+    pre = pretruncation(Theta, cell, can['lam'], cfg.D)
+    a_list = [double_layer(x) for x in pretruncated_sites(Theta, cell, pre)]
+    st, _, _, _ = ctmrg(cell, a_list, cfg.chi, 0.0, ctm_iters, env=env)
+    out = {}
+    for e in link_list(cell):
+        N4 = bond_env(st, cell, e, Theta, pre)
+        norm = np.einsum('ccee->', N4)
+        out[e] = psd_project(N4 / norm) if abs(norm) > 0.0 else N4
+    return out, st.env
+
+
+def env_change(N_new, N_old):
+    """max over links of ||N_new - N_old||_F / ||N_old||_F."""
+    return max(np.linalg.norm(N_new[e] - N_old[e]) / np.linalg.norm(N_old[e]) for e in N_old)
+
+
+def evolve_threshold(A, cell, cfg, n_steps, eps=1e-8, check_every=1, max_window=50, env=None, log=None):
+    """Recycling with the threshold trigger (the reading of "recycled until the bond-environment
+    change exceeds eps"): a window starts with an environment computation (a plain step, whose
+    normalised bond environments N_0 are kept) and continues with recycled steps from A_0 with
+    the window's renormalised gate; after every check_every recycled steps one warm CTMRG
+    iteration on the current state gives its bond environments N, and the window ends (the
+    next step recomputes the environment) once env_change(N, N_0) > eps, or after max_window
+    steps.  Returns (A, env, number of environment computations, number of checks).
+    """
+    g = ipepo(cfg.h, cfg.tau)
+    done, n_env, n_chk = 0, 0, 0
+    while done < n_steps:
+        At, env, info = fu_step(A, cell, cfg, env, g)
+        n_env += 1
+        N0 = {}
+        for e in link_list(cell):                     # the N the ALS of this step used
+            N4 = bond_env(info['state'], cell, e, info['Theta'], info['pre'])
+            norm = np.einsum('ccee->', N4)
+            N0[e] = psd_project(N4 / norm) if abs(norm) > 0.0 else N4
+        can1 = canonicalize(At, cell, cfg.canon_tol, cfg.canon_max)
+        W0 = gauge_start(cell, info['fu'], can1['maps'], cfg.D)
+        W, F, _ = gauge_fix(info['A0'], can1['A'], cell, cfg.gauge_tol, cfg.gauge_max, W0=W0)
+        K = gate_legs(cell, info['fu'], can1['maps'], W)
+        A = info['A0']
+        k = 0
+        while done < n_steps and k < max_window:
+            A = recycled_step(A, cell, g, K)
+            k += 1
+            done += 1
+            if k % check_every == 0 and done < n_steps:
+                N, env = bond_envs(A, cell, cfg, env, g)
+                n_chk += 1
+                d = env_change(N, N0)
+                if log is not None:
+                    log.append(dict(step=done, change=d, F=F))
+                if d > eps:
+                    break
+    return A, env, n_env, n_chk
 
 
 def energy(A, cell, cfg, env=None, tol=1e-10, max_iter=500):

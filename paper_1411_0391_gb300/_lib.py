@@ -37,13 +37,18 @@ class tn_step_report(ctypes.Structure):
                 ("als_iters", c_int * 8), ("als_cost", c_double * 8)]
 
 
+TN_RECYCLE_OFF, TN_RECYCLE_FIXED, TN_RECYCLE_THRESHOLD = 0, 1, 2
+
+
 class tn_evolve_opts(ctypes.Structure):
-    _fields_ = [("recycle", c_int), ("n_re", c_int), ("ctm_tol", c_double), ("ctm_max", c_int)]
+    _fields_ = [("recycle", c_int), ("n_re", c_int), ("ctm_tol", c_double), ("ctm_max", c_int),
+                ("recycle_eps", c_double), ("check_every", c_int)]
 
 
 class tn_evolve_report(ctypes.Structure):
     _fields_ = [("steps", c_int), ("env_computations", c_int), ("ctm_iterations", c_int),
-                ("ctm_moves", c_int), ("nonconverged", c_int), ("last_fidelity", c_double)]
+                ("ctm_moves", c_int), ("nonconverged", c_int), ("last_fidelity", c_double),
+                ("checks", c_int), ("last_change", c_double)]
 
 
 class tn_observables(ctypes.Structure):
@@ -319,12 +324,18 @@ class Context:
         _check(lib().tn_recycle(self.handle, n_re, byref(F)), "tn_recycle")
         return F.value
 
-    def tn_evolve(self, n_steps, recycle=False, n_re=1, ctm_tol=1e-10, ctm_max=500):
-        o = tn_evolve_opts(int(recycle), n_re, ctm_tol, ctm_max)
+    def tn_evolve(self, n_steps, recycle=False, n_re=1, ctm_tol=1e-10, ctm_max=500, recycle_eps=None,
+                  check_every=1):
+        """recycle: False/True (fixed windows of n_re) or "threshold" (windows of at most n_re,
+        ended when the bond environment drifts by more than recycle_eps)."""
+        mode = TN_RECYCLE_THRESHOLD if recycle == "threshold" else (TN_RECYCLE_FIXED if recycle else TN_RECYCLE_OFF)
+        eps = float("inf") if recycle_eps is None else recycle_eps
+        o = tn_evolve_opts(mode, n_re, ctm_tol, ctm_max, eps, check_every)
         rep = tn_evolve_report()
         _check(lib().tn_evolve(self.handle, n_steps, byref(o), byref(rep)), "tn_evolve")
         return dict(steps=rep.steps, env_computations=rep.env_computations, ctm_iterations=rep.ctm_iterations,
-                    ctm_moves=rep.ctm_moves, nonconverged=rep.nonconverged, last_fidelity=rep.last_fidelity)
+                    ctm_moves=rep.ctm_moves, nonconverged=rep.nonconverged, last_fidelity=rep.last_fidelity,
+                    checks=rep.checks, last_change=rep.last_change)
 
     def tn_set_projector_cutoff(self, cut):
         _check(lib().tn_set_projector_cutoff(self.handle, cut), "tn_set_projector_cutoff")

@@ -52,6 +52,7 @@ static bool plan(Ctx& c)
         c.W[e] = take((size_t)D * D);
     }
     double* n4 = take(MAXL * nN);
+    c.N4ref = take(MAXL * nN);
     for (int e = 0; e < MAXL; ++e) c.N4[e] = n4 ? n4 + e * nN : nullptr;
     c.g = take(64);
     const size_t nl4 = (size_t)L * L * L * L;
@@ -170,6 +171,7 @@ int tn_set_hamiltonian(void* ctx, double J, double h)
 {
     if (!ctx || !(J > 0.0) || !std::isfinite(h)) return TN_EINVAL;
     C(ctx)->J = J; C(ctx)->h = h;
+    C(ctx)->have_gate = false;            // the gate of a recycling window belongs to the old g
     if (C(ctx)->tau > 0.0) return build_pepo(*C(ctx));
     return TN_OK;
 }
@@ -178,6 +180,7 @@ int tn_set_time_step(void* ctx, double tau)
 {
     if (!ctx || !(tau > 0.0) || !std::isfinite(tau)) return TN_EINVAL;
     C(ctx)->tau = tau;
+    C(ctx)->have_gate = false;
     return build_pepo(*C(ctx));
 }
 
@@ -191,6 +194,7 @@ int tn_set_state(void* ctx, const double* host, size_t n)
         TN_CUDA(cudaMemcpyAsync(c.A[t], host + t * per, per * sizeof(double), cudaMemcpyHostToDevice, c.st));
     TN_CUDA(cudaStreamSynchronize(c.st));
     c.have_state = true;
+    c.have_gate = false;
     return TN_OK;
 }
 
@@ -379,13 +383,65 @@ int tn_recycle(void* ctx, int n_re, double* fidelity)
     return TN_OK;
 }
 
+// Recycling with the threshold trigger: a window starts with an environment
+// computation (a plain step; its bond environments N_0 are kept) and continues
+// with recycled steps from A_0; after every check_every steps one warm CTMRG
+// iteration on the current state gives its bond environments N (a8), and the
+// window ends once max_links ||N - N_0||_F / ||N_0||_F > eps, or after n_re steps.
+static int evolve_threshold(Ctx& c, void* ctx, int n_steps, const tn_evolve_opts* o, tn_evolve_report& r)
+{
+    const int k = c.kD;
+    const size_t n4 = (size_t)k * k * k * k;
+    int done = 0;
+    while (done < n_steps) {
+        tn_step_report sr{};
+        int s = tn_fu_step(ctx, o->ctm_tol, o->ctm_max, &sr);
+        if (s == TN_ENOCONV) r.nonconverged++;
+        else if (s != TN_OK) return s;
+        r.env_computations++;
+        r.ctm_iterations += sr.ctm_iterations;
+        TN_CUDA(cudaMemcpyAsync(c.N4ref, c.N4[0], sizeof(double) * n4 * c.nl, cudaMemcpyDeviceToDevice, c.st));
+        double F = 0.0;
+        TN_TRY(recycle_build(c, &F));
+        r.last_fidelity = F;
+        for (int w = 1; done < n_steps && w <= o->n_re; ++w) {
+            TN_TRY(recycle_advance(c, 1));
+            ++done;
+            if (w % o->check_every != 0 || done >= n_steps) continue;
+            TN_TRY(step_prepare(c, nullptr));
+            tn_ctm_report cr{};
+            int cs = ctmrg_iterations(c, 0.0, 1, &cr);
+            if (cs != TN_OK && cs != TN_ENOCONV) return cs;
+            r.ctm_iterations += 1;
+            TN_TRY(bond_envs_psd(c));
+            c.prepared = false;
+            double d = 0.0;
+            TN_TRY(env_change(c, &d));
+            r.checks++;
+            r.last_change = d;
+            if (!(d <= o->recycle_eps)) break;
+        }
+    }
+    r.steps = done;
+    return TN_OK;
+}
+
 int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* o, tn_evolve_report* rep)
 {
     if (!ctx || !o || n_steps < 0) return TN_EINVAL;
-    if (o->recycle && o->n_re < 1) return TN_EINVAL;
+    if (o->recycle < TN_RECYCLE_OFF || o->recycle > TN_RECYCLE_THRESHOLD) return TN_EINVAL;
+    if (o->recycle != TN_RECYCLE_OFF && o->n_re < 1) return TN_EINVAL;
+    if (o->recycle == TN_RECYCLE_THRESHOLD && (o->check_every < 1 || o->recycle_eps != o->recycle_eps))
+        return TN_EINVAL;
     Ctx& c = *C(ctx);
     tn_evolve_report r{};
     long long moves0 = c.ctm_moves;
+    if (o->recycle == TN_RECYCLE_THRESHOLD) {
+        TN_TRY(evolve_threshold(c, ctx, n_steps, o, r));
+        r.ctm_moves = (int)(c.ctm_moves - moves0);
+        if (rep) *rep = r;
+        return TN_OK;
+    }
     int done = 0;
     while (done < n_steps) {
         tn_step_report sr{};

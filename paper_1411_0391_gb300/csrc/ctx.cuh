@@ -36,6 +36,7 @@ struct Ctx {
     int D = 0, chi = 0, kD = 0, leg = 0;   // leg: dimension of a double-layer leg
     double J = 1.0, h = 0.0, tau = 0.0;
     bool have_state = false, have_network = false, have_pepo = false, prepared = false, updated = false;
+    bool have_gate = false;    // the leg matrices K of a recycling window are built
 
     // state and step tensors
     double* A[MAXT];
@@ -49,6 +50,7 @@ struct Ctx {
     double* preP[MAXL];
     double* preQ[MAXL];
     double* N4[MAXL];
+    double* N4ref = nullptr;   // bond environments at the start of a recycling window (all links)
     double* fuP[MAXL];
     double* fuQ[MAXL];
     double* W[MAXL];
@@ -116,6 +118,10 @@ int step_prepare(Ctx& c, tn_step_report* rep);
 int step_update(Ctx& c, tn_step_report* rep);
 int su_step(Ctx& c, tn_step_report* rep);
 int recycle(Ctx& c, int n_re, double* F);
+int recycle_build(Ctx& c, double* F);
+int recycle_advance(Ctx& c, int n_re);
+int bond_envs_psd(Ctx& c);
+int env_change(Ctx& c, double* out);
 int measure(Ctx& c, tn_observables* obs);
 
 }  // namespace tn

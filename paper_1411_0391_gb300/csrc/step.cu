@@ -1124,10 +1124,12 @@ int su_step(Ctx& c, tn_step_report* rep)
     return TN_OK;
 }
 
-int step_update(Ctx& c, tn_step_report* rep)
+// Bond environments of every link type (a8) into c.N4, normalised by <g|g>,
+// symmetrised and projected on their positive part; empty[e] flags <g|g> = 0.
+int bond_envs_psd(Ctx& c)
 {
     if (!c.prepared) return TN_ESTATE;
-    const int k = c.kD, n4 = k * k * k * k;
+    const int k = c.kD;
     for (int e = 0; e < c.nl; ++e) TN_TRY(bond_env(c, e, c.N4[e]));                    // a8
     int* empty = (int*)(c.dscratch + 8);
     {
@@ -1140,6 +1142,15 @@ int step_update(Ctx& c, tn_step_report* rep)
         psd_kernel<<<c.nl, 512, smem, c.st>>>(c.N4[0], k, empty);
         TN_LAUNCHED();
     }
+    return TN_OK;
+}
+
+int step_update(Ctx& c, tn_step_report* rep)
+{
+    if (!c.prepared) return TN_ESTATE;
+    const int k = c.kD, n4 = k * k * k * k;
+    TN_TRY(bond_envs_psd(c));                                                            // a8
+    int* empty = (int*)(c.dscratch + 8);
     AlsArgs aa;                                                                          // a9
     aa.N4 = c.N4[0];
     aa.empty = empty;
@@ -1177,7 +1188,9 @@ int step_update(Ctx& c, tn_step_report* rep)
     return TN_OK;
 }
 
-int recycle(Ctx& c, int n_re, double* F)
+// Steps (i)-(iii) of the window: A_0, canonical form of A~, gauge fix, leg
+// matrices K; the state is reset to A_0.
+int recycle_build(Ctx& c, double* F)
 {
     if (!c.updated) return TN_ESTATE;
     const int D = c.D;
@@ -1220,9 +1233,22 @@ int recycle(Ctx& c, int n_re, double* F)
     gt.D = D;
     gate_kernel<<<4 * c.nt, 64, 0, c.st>>>(gt);
     TN_LAUNCHED();
-    // the window: A_k = (g A_{k-1}) x_legs K, from A_0
     for (int t = 0; t < c.nt; ++t)
         TN_CUDA(cudaMemcpyAsync(c.A[t], c.A0[t], sizeof(double) * 2 * D * D * D * D, cudaMemcpyDeviceToDevice, c.st));
+    if (F) {
+        TN_CUDA(cudaMemcpyAsync(F, c.dscratch + 32, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+        TN_CUDA(cudaStreamSynchronize(c.st));
+    }
+    c.updated = false;
+    c.have_gate = true;
+    return TN_OK;
+}
+
+// n recycled steps with the window's gate: A <- (g A) x_legs K, max-abs normalised.
+int recycle_advance(Ctx& c, int n_re)
+{
+    if (!c.have_gate) return TN_ESTATE;
+    const int D = c.D;
     for (int r = 0; r < n_re; ++r)
         for (int t = 0; t < c.nt; ++t) {
             TN_TRY(apply_pepo(c, c.A[t], c.Theta[t]));
@@ -1242,11 +1268,46 @@ int recycle(Ctx& c, int n_re, double* F)
             TN_TRY(normalize_maxabs(c.st, c.A[t], 2LL * D * D * D * D, 1, 0));
             c.ar.release(mk);
         }
-    if (F) {
-        TN_CUDA(cudaMemcpyAsync(F, c.dscratch + 32, sizeof(double), cudaMemcpyDeviceToHost, c.st));
-        TN_CUDA(cudaStreamSynchronize(c.st));
+    return TN_OK;
+}
+
+int recycle(Ctx& c, int n_re, double* F)
+{
+    TN_TRY(recycle_build(c, F));
+    return recycle_advance(c, n_re);
+}
+
+// change[0] = max over link types of ||N4 - ref||_F / ||ref||_F (one block per link)
+__global__ void env_change_kernel(const double* __restrict__ N4, const double* __restrict__ ref, int n4, int nl,
+                                  double* __restrict__ change)
+{
+    __shared__ double red[32];
+    __shared__ double part[MAXL];
+    for (int e = 0; e < nl; ++e) {
+        double dn = 0.0, rn = 0.0;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+            const double r = ref[(size_t)e * n4 + i], d = N4[(size_t)e * n4 + i] - r;
+            dn = fma(d, d, dn); rn = fma(r, r, rn);
+        }
+        dn = block_sum(dn, red);
+        rn = block_sum(rn, red);
+        if (threadIdx.x == 0) part[e] = rn > 0.0 ? sqrt(dn / rn) : (dn > 0.0 ? INFINITY : 0.0);
     }
-    c.updated = false;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int e = 0; e < nl; ++e) m = fmax(m, part[e]);
+        change[0] = m;
+    }
+}
+
+int env_change(Ctx& c, double* out)
+{
+    const int k = c.kD, n4 = k * k * k * k;
+    env_change_kernel<<<1, 256, 0, c.st>>>(c.N4[0], c.N4ref, n4, c.nl, c.dscratch + 40);
+    TN_LAUNCHED();
+    TN_CUDA(cudaMemcpyAsync(out, c.dscratch + 40, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    TN_CUDA(cudaStreamSynchronize(c.st));
     return TN_OK;
 }
 

@@ -153,3 +153,22 @@ def test_d1_mean_field_on_gpu():
     ctx.tn_evolve(200, ctm_tol=1e-10, ctm_max=200)
     g = _gpu_energy(ctx)
     assert abs(g['e_site'] - (-2.0 - h * h / 8.0)) < 1e-4
+
+
+@pytest.mark.parametrize("eps,check_every,n_env_expected", [(float("inf"), 1, 1), (1e-14, 1, 4), (float("inf"), 2, 1)])
+def test_threshold_recycling_parity(eps, check_every, n_env_expected):
+    """Recycling with the threshold trigger against the oracle: environment computations,
+    checks and the final energy (D = 2, chi = 8, h = 3, tau = 0.01, four steps)."""
+    D, chi, h, tau, n = 2, 8, 3.0, 0.01, 4
+    A = random_peps(2, D, instance=8)
+    ctx = _ctx(D, chi, h, tau, A)
+    rep = ctx.tn_evolve(n, recycle="threshold", n_re=n, ctm_tol=1e-10, ctm_max=500, recycle_eps=eps,
+                        check_every=check_every)
+    cfg = OR.Config(h=h, tau=tau, D=D, chi=chi, ctm_tol=1e-10, ctm_max=500)
+    Ao, _, n_env, n_chk = OR.evolve_threshold(A, CELL, cfg, n, eps=eps, check_every=check_every, max_window=n)
+    assert rep["env_computations"] == n_env == n_env_expected
+    assert rep["checks"] == n_chk
+    g = _gpu_energy(ctx)
+    o = OR.energy(Ao, CELL, cfg, tol=1e-12)
+    assert abs(g["e_site"] - o["e_site"]) < 1e-9 * abs(o["e_site"])
+    ctx.close()

@@ -121,3 +121,51 @@ def test_su_above_fu_variationally():
     esu = R.energy(Asu, cell, cfg)['e_site']
     efu = R.energy(Afu, cell, cfg, env=env)['e_site']
     assert efu < esu
+
+
+# --- recycling with the threshold trigger ------------------------------------------------
+
+def _thr_setup():
+    cell = C.checkerboard()
+    A = random_peps(2, 2, instance=8)
+    cfg = R.Config(h=3.0, tau=0.01, D=2, chi=8, ctm_tol=1e-10, ctm_max=500)
+    return cell, A, cfg
+
+
+def test_threshold_infinite_eps_is_one_fixed_window():
+    """eps = inf never ends the window: the same state as one window of N_Re = n steps."""
+    cell, A, cfg = _thr_setup()
+    n = 4
+    At, _, n_env, n_chk = R.evolve_threshold(A, cell, cfg, n, eps=np.inf, check_every=1, max_window=n)
+    Aw, _, _ = R.recycle_window(A, cell, cfg, n)
+    assert n_env == 1 and n_chk == n - 1
+    for x, y in zip(At, Aw):
+        np.testing.assert_allclose(x, y, rtol=0, atol=1e-12)
+
+
+def test_threshold_zero_eps_is_the_plain_trajectory():
+    """eps = 0 ends every window after one recycled step, which reproduces the plain step up
+    to a gauge.  That gauge is not orthogonal, and the chi-truncated CTMRG of the next steps
+    is covariant only under orthogonal gauges, so the trajectories agree to the truncation
+    level (5e-7 at chi = 8), not to rounding."""
+    cell, A, cfg = _thr_setup()
+    n = 3
+    At, env_t, n_env, n_chk = R.evolve_threshold(A, cell, cfg, n, eps=0.0, check_every=1)
+    Ap, env_p, _ = R.evolve(A, cell, cfg, n)
+    assert n_env == n and n_chk == n - 1
+    et = R.energy(At, cell, cfg, tol=1e-12)['e_site']
+    ep = R.energy(Ap, cell, cfg, tol=1e-12)['e_site']
+    assert abs(et - ep) < 2e-6 * abs(ep)
+
+
+def test_threshold_trigger_limits():
+    """Every check exceeds a tiny threshold (one environment computation per step); none
+    exceeds an infinite one (one for the whole run); the log records each check's change."""
+    cell, A, cfg = _thr_setup()
+    n = 4
+    log = []
+    _, _, n_env, n_chk = R.evolve_threshold(A, cell, cfg, n, eps=1e-14, check_every=1, log=log)
+    assert n_env == n and n_chk == n - 1
+    assert all(d['change'] > 1e-14 for d in log)
+    _, _, n_env, n_chk = R.evolve_threshold(A, cell, cfg, n, eps=np.inf, check_every=2, max_window=n)
+    assert n_env == 1 and n_chk == 1
