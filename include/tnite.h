@@ -191,6 +191,10 @@ typedef struct tn_evolve_opts {
                               N: those of the current state after one warm CTMRG
                               iteration, both normalised and positive as in a8) */
     int    check_every;    /* THRESHOLD: recycled steps between checks (>= 1) */
+    int    warmup_plain;   /* plain full-update steps before the first recycling
+                              window (counted in n_steps) */
+    double als_tol;        /* ALS stop (relative change of PQ); <= 0: 1e-12 */
+    int    als_max;        /* ALS sweep cap; <= 0: 50 */
 } tn_evolve_opts;
 
 typedef struct tn_evolve_report {
@@ -206,8 +210,10 @@ typedef struct tn_evolve_report {
 
 /* n_steps imaginary-time steps (Sec. VI.B-C).  The threshold mode is the
  * reading of "the environment recycled until the bond-environment change
- * exceeds eps" (the paper itself uses a fixed N_Re).  TN_EINVAL for an
- * unknown mode, n_re < 1 when recycling, check_every < 1 or a NaN eps. */
+ * exceeds eps" (the paper itself uses a fixed N_Re).  The ALS settings stay
+ * in force for later tn_fu_step / tn_step_update calls.  TN_EINVAL for an
+ * unknown mode, n_re < 1 when recycling, check_every < 1, a NaN eps or a
+ * negative warmup_plain. */
 int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* opts, tn_evolve_report* rep);
 
 /* ---- observables (Sec. VI.D; row a14) ----------------------------------- */

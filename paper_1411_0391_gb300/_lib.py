@@ -42,7 +42,8 @@ TN_RECYCLE_OFF, TN_RECYCLE_FIXED, TN_RECYCLE_THRESHOLD = 0, 1, 2
 
 class tn_evolve_opts(ctypes.Structure):
     _fields_ = [("recycle", c_int), ("n_re", c_int), ("ctm_tol", c_double), ("ctm_max", c_int),
-                ("recycle_eps", c_double), ("check_every", c_int)]
+                ("recycle_eps", c_double), ("check_every", c_int), ("warmup_plain", c_int),
+                ("als_tol", c_double), ("als_max", c_int)]
 
 
 class tn_evolve_report(ctypes.Structure):
@@ -325,12 +326,12 @@ class Context:
         return F.value
 
     def tn_evolve(self, n_steps, recycle=False, n_re=1, ctm_tol=1e-10, ctm_max=500, recycle_eps=None,
-                  check_every=1):
+                  check_every=1, warmup_plain=0, als_tol=1e-12, als_max=50):
         """recycle: False/True (fixed windows of n_re) or "threshold" (windows of at most n_re,
         ended when the bond environment drifts by more than recycle_eps)."""
         mode = TN_RECYCLE_THRESHOLD if recycle == "threshold" else (TN_RECYCLE_FIXED if recycle else TN_RECYCLE_OFF)
         eps = float("inf") if recycle_eps is None else recycle_eps
-        o = tn_evolve_opts(mode, n_re, ctm_tol, ctm_max, eps, check_every)
+        o = tn_evolve_opts(mode, n_re, ctm_tol, ctm_max, eps, check_every, warmup_plain, als_tol, als_max)
         rep = tn_evolve_report()
         _check(lib().tn_evolve(self.handle, n_steps, byref(o), byref(rep)), "tn_evolve")
         return dict(steps=rep.steps, env_computations=rep.env_computations, ctm_iterations=rep.ctm_iterations,

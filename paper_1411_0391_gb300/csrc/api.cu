@@ -433,16 +433,30 @@ int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* o, tn_evolve_report*
     if (o->recycle != TN_RECYCLE_OFF && o->n_re < 1) return TN_EINVAL;
     if (o->recycle == TN_RECYCLE_THRESHOLD && (o->check_every < 1 || o->recycle_eps != o->recycle_eps))
         return TN_EINVAL;
+    if (o->warmup_plain < 0) return TN_EINVAL;
     Ctx& c = *C(ctx);
+    c.als_tol = o->als_tol > 0.0 ? o->als_tol : 1e-12;
+    c.als_max = o->als_max > 0 ? o->als_max : 50;
     tn_evolve_report r{};
     long long moves0 = c.ctm_moves;
+    int done = 0;
+    // warm-up: plain steps first (the recycled windows start from an evolved state)
+    const int warm = o->recycle == TN_RECYCLE_OFF ? 0 : std::min(o->warmup_plain, n_steps);
+    for (; done < warm; ++done) {
+        tn_step_report sr{};
+        int s = tn_fu_step(ctx, o->ctm_tol, o->ctm_max, &sr);
+        if (s == TN_ENOCONV) r.nonconverged++;
+        else if (s != TN_OK) return s;
+        r.env_computations++;
+        r.ctm_iterations += sr.ctm_iterations;
+    }
     if (o->recycle == TN_RECYCLE_THRESHOLD) {
-        TN_TRY(evolve_threshold(c, ctx, n_steps, o, r));
+        TN_TRY(evolve_threshold(c, ctx, n_steps - done, o, r));
+        r.steps += done;
         r.ctm_moves = (int)(c.ctm_moves - moves0);
         if (rep) *rep = r;
         return TN_OK;
     }
-    int done = 0;
     while (done < n_steps) {
         tn_step_report sr{};
         int s = tn_fu_step(ctx, o->ctm_tol, o->ctm_max, &sr);

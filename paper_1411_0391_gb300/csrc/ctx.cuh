@@ -35,6 +35,8 @@ struct Ctx {
     int pat[4][4];
     int D = 0, chi = 0, kD = 0, leg = 0;   // leg: dimension of a double-layer leg
     double J = 1.0, h = 0.0, tau = 0.0;
+    double als_tol = 1e-12;    // ALS stop: ||M_new - M|| <= als_tol ||M|| (reading of Sec. VI.B)
+    int als_max = 50;
     bool have_state = false, have_network = false, have_pepo = false, prepared = false, updated = false;
     bool have_gate = false;    // the leg matrices K of a recycling window are built
 

@@ -1160,8 +1160,8 @@ int step_update(Ctx& c, tn_step_report* rep)
     aa.iters = iters;
     aa.cost = cost;
     aa.D = c.D;
-    aa.tol = 1e-12;
-    aa.max_iter = 50;
+    aa.tol = c.als_tol;
+    aa.max_iter = c.als_max;
     {
         const int nR = k * c.D;
         size_t smem = sizeof(double) * ((size_t)n4 + 3 * (size_t)k * k + 2 * nR + 3 * (size_t)nR * nR + 4 * nR + 2 * (nR / 2 + 1))
