@@ -16,8 +16,13 @@ library primitives:
                                    cost function Eq. (var), ALS Eq. (var1)
     canonical    Sec. IV           iPEPS canonical form Eqs. (17)-(20) and
                                    gauge fixing by local fidelity Eq. (25)
-    recycle      Sec. VI.C         renormalised gate and recycled steps
+    recycle      Sec. VI.C         renormalised gate and recycled steps (fixed
+                                   windows and the threshold trigger), the
+                                   simple-update step of the Sec. VI.D comparison
     observables  Sec. VI.D         m_z, energy per site/link
+    gradient     (beyond the paper) energy gradient of the 1-site iPEPS by
+                                   central differences, the reference for a
+                                   CTMRG fixed-point adjoint
     imps         Sec. III, V       1D canonical form, gauge fix, recycling
     classical    (pin only)        2D classical Ising network for CTMRG pins
     ed           (pin only)        exact diagonalisation on small tori
