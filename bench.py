@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--profile-moves", type=int, default=0,
                    help="run only this many CTMRG moves and one update at the workload shape (for ncu)")
     p.add_argument("--profile-precision", default="tf32x3", choices=sorted(PRECISIONS))
+    p.add_argument("--profile-recycle", type=int, default=0,
+                   help="with --profile-moves: after the update, one recycling window of this many steps "
+                        "and one simple-update step")
     p.add_argument("--profile-gemm", action="store_true",
                    help="run only the N x N x N products of the workload (tcgen05 TF32x3 and FP64), 3 launches each")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -343,9 +346,13 @@ def run_gpu(args):
         ctx.tn_step_prepare()
         ctx.tn_ctmrg_moves(args.profile_moves)
         ctx.tn_step_update()
+        if args.profile_recycle:
+            ctx.tn_recycle(args.profile_recycle)
+            ctx.tn_su_step()
         torch.cuda.synchronize()
         print(json.dumps({"profile_moves": args.profile_moves, "precision": args.profile_precision,
-                          "skip": skip, "launches": L.tn_launch_count() - skip}))
+                          "profile_recycle": args.profile_recycle, "skip": skip,
+                          "launches": L.tn_launch_count() - skip}))
         return
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)       # larger than the 129 MB L2
