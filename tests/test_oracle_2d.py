@@ -138,3 +138,42 @@ def test_recycling_window_nre1_matches_plain_step():
     assert abs(mp['e_site'] - mr['e_site']) < 1e-9
     for t in range(2):
         assert abs(mp['mx'][t] - mr['mx'][t]) < 1e-9
+
+
+def test_bond_env_of_product_state_factorises():
+    """Row a8 pinned directly: at D = 1 the state is a product and the chi = 1 CTMRG is
+    exact, so the environment of a link is the tensor product of the two sites' Gram
+    matrices of their open link legs (all other legs of Theta pre-truncated to D = 1):
+    N[a, b, a', b'] = G_p[a, a'] G_q[b, b'] up to the scale of the environment."""
+    from oracle import fullupdate as FU
+    from oracle import model as MD
+    from oracle import canonical as CN
+    cell = C.checkerboard()
+    A = random_peps(2, 1, instance=2)
+    g = MD.ipepo(3.0, 0.05)
+    can = CN.canonicalize(A, cell)
+    Theta = [MD.apply_pepo(g, a) for a in can['A']]
+    pre = FU.pretruncation(Theta, cell, can['lam'], 1)
+    a_list = [C.double_layer(x) for x in FU.pretruncated_sites(Theta, cell, pre)]
+    st, _, _, conv = C.ctmrg(cell, a_list, 1, 1e-13, 200)
+    _, _, pos = FU.neighbours(cell)
+
+    def gram(T, leg):
+        Tm = np.moveaxis(T, FU.LEG[leg], -1)
+        Tm = Tm.reshape(-1, Tm.shape[-1])
+        return Tm.T @ Tm
+
+    for e in FU.link_list(cell):
+        t, dr = e
+        x, y = pos[t]
+        if dr == 'h':
+            tq, lp, lq = cell.tid(x + 1, y), 'r', 'l'
+        else:
+            tq, lp, lq = cell.tid(x, y + 1), 'd', 'u'
+        Gp = gram(FU.truncate_legs(Theta[t], cell, t, pre, lp), lp)
+        Gq = gram(FU.truncate_legs(Theta[tq], cell, tq, pre, lq), lq)
+        N4 = FU.bond_env(st, cell, e, Theta, pre)
+        ref = np.einsum('ac,bd->abcd', Gp, Gq)
+        N4 = N4 / np.einsum('ccee->', N4)
+        ref = ref / np.einsum('ccee->', ref)
+        np.testing.assert_allclose(N4, ref, rtol=0, atol=1e-12)
