@@ -192,3 +192,26 @@ def test_evolve_warmup_then_fixed_windows():
     o = OR.energy(Ao, CELL, cfg, tol=1e-12)
     assert abs(g["e_site"] - o["e_site"]) < 1e-7 * abs(o["e_site"])
     ctx.close()
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_pretruncation_projectors(D):
+    """Row a7: the lambda-weighted simple-update projectors of every link type, compared
+    through the singular values of P Q (kappa D x kappa D, rank D): the two canonical
+    forms may differ by a sign or orthogonal gauge on the bond, which acts on P Q by an
+    orthogonal similarity."""
+    A = random_peps(2, D, instance=5)
+    ctx = _ctx(D, 8, 3.0, 0.01, A)
+    ctx.tn_step_prepare()
+    can = __import__("oracle.canonical", fromlist=["canonicalize"]).canonicalize(A, CELL)
+    Theta = [OM.apply_pepo(OM.ipepo(3.0, 0.01), a) for a in can['A']]
+    pre = OF.pretruncation(Theta, CELL, can['lam'], D)
+    k = 2 * D
+    for e, link in enumerate(OF.link_list(CELL)):
+        P = ctx.tn_get_tensor(L.TN_T_PRE_P, e, (k, D))
+        Q = ctx.tn_get_tensor(L.TN_T_PRE_Q, e, (D, k))
+        Po, Qo = pre[link]
+        s_gpu = np.linalg.svd(P @ Q, compute_uv=False)
+        s_ref = np.linalg.svd(Po @ Qo, compute_uv=False)
+        np.testing.assert_allclose(s_gpu, s_ref, rtol=0, atol=1e-9 * s_ref[0])
+    ctx.close()
