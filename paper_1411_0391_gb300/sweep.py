@@ -12,31 +12,47 @@ from .inputs import random_peps
 
 
 def run_field(h, D, chi, tau, steps, method="fu", n_re=1, ctm_tol=1e-8, ctm_max=200, measure_tol=1e-9,
-              measure_max=300, precision=L.TN_F64, instance=0, device="cuda:0", state=None):
+              measure_max=300, precision=L.TN_F64, instance=0, device="cuda:0", state=None, recycle_eps=None,
+              check_every=1, warmup_plain=0):
     """Evolve one field value and measure it; returns a dict of observables.
 
-    method: "fu" (full update, recycled in windows of n_re steps when n_re > 1)
-    or "su" (simple update).  The measurement converges a fresh CTMRG.
+    method: "fu" (full update: plain; recycled in windows of n_re steps when
+    n_re > 1; or, with recycle_eps, windows of at most n_re steps ended when the
+    bond environment drifts by more than recycle_eps) or "su" (simple update).
+    tau, steps: one time step and count, or lists for a schedule of stages
+    (e.g. tau = [0.01, 0.001], steps = [1000, 1000]).  The measurement converges
+    a fresh CTMRG.
     """
+    taus = list(tau) if isinstance(tau, (list, tuple)) else [tau]
+    counts = list(steps) if isinstance(steps, (list, tuple)) else [steps]
+    if len(taus) != len(counts):
+        raise ValueError("tau and steps stages differ in length")
     ctx = L.Context(D, chi, device=device, precision=precision)
     try:
         ctx.tn_set_hamiltonian(1.0, h)
-        ctx.tn_set_time_step(tau)
         ctx.tn_set_state(state if state is not None else random_peps(2, D, instance=instance))
         n_env = 0
-        if method == "su":
-            for _ in range(steps):
-                ctx.tn_su_step()
-        elif method == "fu":
-            rep = ctx.tn_evolve(steps, recycle=n_re > 1, n_re=max(n_re, 1), ctm_tol=ctm_tol, ctm_max=ctm_max)
-            n_env = rep["env_computations"]
-        else:
-            raise ValueError("method must be 'fu' or 'su'")
+        for stage, (tau_s, n_s) in enumerate(zip(taus, counts)):
+            ctx.tn_set_time_step(tau_s)
+            if method == "su":
+                for _ in range(n_s):
+                    ctx.tn_su_step()
+            elif method == "fu":
+                if recycle_eps is not None:
+                    mode = "threshold"
+                else:
+                    mode = n_re > 1
+                rep = ctx.tn_evolve(n_s, recycle=mode, n_re=max(n_re, 1), ctm_tol=ctm_tol, ctm_max=ctm_max,
+                                    recycle_eps=recycle_eps, check_every=check_every,
+                                    warmup_plain=warmup_plain if stage == 0 else 0)
+                n_env += rep["env_computations"]
+            else:
+                raise ValueError("method must be 'fu' or 'su'")
         ctx.tn_build_double_layer()
         ctx.tn_reset_env()
         crep = ctx.tn_ctmrg(measure_tol, measure_max)
         m = ctx.tn_measure()
-        return dict(h=h, method=method, D=D, chi=chi, tau=tau, steps=steps, n_re=n_re, e_site=m["e_site"],
+        return dict(h=h, method=method, D=D, chi=chi, tau=taus, steps=counts, n_re=n_re, e_site=m["e_site"],
                     mx=sum(m["mx"]) / len(m["mx"]), mz=sum(abs(z) for z in m["mz"]) / len(m["mz"]),
                     env_computations=n_env, ctm_converged=crep["converged"], state=ctx.tn_get_state())
     finally:
