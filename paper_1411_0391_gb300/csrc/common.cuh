@@ -3,6 +3,7 @@
 // carved from the caller's workspace; nothing here calls cudaMalloc.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 #include <cstring>
@@ -17,6 +18,23 @@ void tn_last_cuda_error(cudaError_t e);
 void tn_count_launch();
 // after every kernel launch: count it and surface launch errors
 #define TN_LAUNCHED() do { tn_count_launch(); TN_CUDA(cudaGetLastError()); } while (0)
+
+// Opt `kernel` into `bytes` of dynamic shared memory on the current device.
+// The attribute belongs to the device, so the record of where it has been set
+// (`done`, bit d for device d < 64) is per device; devices >= 64 set it on every
+// call.  Setting it twice is harmless, so racing threads need no lock.
+template <typename K>
+inline cudaError_t tn_smem_optin(K kernel, int bytes, std::atomic<unsigned long long>& done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 // Counter-based uniform number in [-1, 1): splitmix64 of (seed, index).
 __host__ __device__ inline double tn_hash_uniform(unsigned long long seed, long long i)

@@ -44,12 +44,8 @@ int svd_small(cudaStream_t st, const double* A, int m, int n, int batch, double*
 {
     if (n < 1 || m < n || m > SMALL_MAX || batch < 1) return TN_EINVAL;
     size_t smem = svd_smem(m, n);
-    static bool attr = false;
-    if (!attr) {
-        TN_CUDA(cudaFuncSetAttribute(svd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)svd_smem(SMALL_MAX, SMALL_MAX)));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(svd_small_kernel, (int)svd_smem(SMALL_MAX, SMALL_MAX), attr));
     svd_small_kernel<<<batch, 512, smem, st>>>(A, m, n, U, S, V, 60);
     TN_LAUNCHED();
     return TN_OK;
@@ -79,12 +75,8 @@ static size_t eigh_smem(int n) { return sizeof(double) * (2 * (size_t)n * n + 2 
 int eigh_small(cudaStream_t st, const double* A, int n, int batch, double* W, double* V)
 {
     if (n < 1 || n > SMALL_MAX || batch < 1) return TN_EINVAL;
-    static bool attr = false;
-    if (!attr) {
-        TN_CUDA(cudaFuncSetAttribute(eigh_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)eigh_smem(SMALL_MAX)));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(eigh_small_kernel, (int)eigh_smem(SMALL_MAX), attr));
     eigh_small_kernel<<<batch, 512, eigh_smem(n), st>>>(A, n, W, V, 60);
     TN_LAUNCHED();
     return TN_OK;
@@ -117,12 +109,8 @@ static size_t chol_smem(int n) { return sizeof(double) * 2 * (size_t)n * n + siz
 int chol_inv(cudaStream_t st, const double* G, int n, double c_shift, double* X)
 {
     if (n < 1 || n > SMALL_MAX) return TN_EINVAL;
-    static bool attr = false;
-    if (!attr) {
-        TN_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)chol_smem(SMALL_MAX)));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(chol_inv_kernel, (int)chol_smem(SMALL_MAX), attr));
     chol_inv_kernel<<<1, 512, chol_smem(n), st>>>(G, n, c_shift, X);
     TN_LAUNCHED();
     return TN_OK;

@@ -306,14 +306,10 @@ size_t svd32_smem(int n) { return sizeof(float) * 2 * (size_t)n * n + 64; }
 int orth_mixed(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, int fixes)
 {
     if (cols < 1 || cols > SMALL_MAX) return TN_EINVAL;
-    static bool attr = false;
-    if (!attr) {
-        TN_CUDA(cudaFuncSetAttribute(chol32_whiten_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)chol32_smem(SMALL_MAX)));
-        TN_CUDA(cudaFuncSetAttribute(orth_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)orthfix_smem(SMALL_MAX)));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr0{0};
+    static std::atomic<unsigned long long> attr1{0};
+    TN_CUDA(tn_smem_optin(chol32_whiten_kernel, (int)chol32_smem(SMALL_MAX), attr0));
+    TN_CUDA(tn_smem_optin(orth_fix_kernel, (int)orthfix_smem(SMALL_MAX), attr1));
     size_t mk = ar.mark();
     double* G = ar.take((size_t)cols * cols);
     double* X = ar.take((size_t)cols * cols);
@@ -335,12 +331,8 @@ int orth_mixed(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int
 int svd_mixed(cudaStream_t st, Arena& ar, const double* B, int n, double* U, double* S, double* V, int steps)
 {
     if (n < 1 || n > SMALL_MAX) return TN_EINVAL;
-    static bool attr = false;
-    if (!attr) {
-        TN_CUDA(cudaFuncSetAttribute(svd32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)svd32_smem(SMALL_MAX)));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(svd32_kernel, (int)svd32_smem(SMALL_MAX), attr));
     size_t mk = ar.mark();
     const size_t nn = (size_t)n * n;
     double* Rm = ar.take(nn);

@@ -447,11 +447,8 @@ int canonicalize(Ctx& c, double* const* A, double* const* Aout, int* iters, bool
     a.iters = di;
     a.delta = c.dscratch + 1;
     size_t smem = canon_smem(c.D, c.nt, c.nl);
-    static bool attr = false;
-    if (!attr) {
-        TN_CUDA(cudaFuncSetAttribute(canon_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(canon_kernel, 200 * 1024, attr));
     if (smem > 200 * 1024) return TN_EINVAL;
     canon_kernel<<<1, 256, smem, c.st>>>(a);
     TN_LAUNCHED();
@@ -1135,8 +1132,8 @@ int bond_envs_psd(Ctx& c)
     {
         const int n = k * k;
         size_t smem = sizeof(double) * (2 * (size_t)n * n + n + 2 * (n / 2 + 1)) + sizeof(int) * 2 * (n / 2 + 1) + 64;
-        static bool attr = false;
-        if (!attr) { TN_CUDA(cudaFuncSetAttribute(psd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); attr = true; }
+        static std::atomic<unsigned long long> attr{0};
+        TN_CUDA(tn_smem_optin(psd_kernel, 200 * 1024, attr));
         if (smem > 200 * 1024) return TN_EINVAL;
         // N4 buffers are consecutive (allocated together)
         psd_kernel<<<c.nl, 512, smem, c.st>>>(c.N4[0], k, empty);
@@ -1166,8 +1163,8 @@ int step_update(Ctx& c, tn_step_report* rep)
         const int nR = k * c.D;
         size_t smem = sizeof(double) * ((size_t)n4 + 3 * (size_t)k * k + 2 * nR + 3 * (size_t)nR * nR + 4 * nR + 2 * (nR / 2 + 1))
                       + sizeof(int) * 2 * (nR / 2 + 1) + 64;
-        static bool attr = false;
-        if (!attr) { TN_CUDA(cudaFuncSetAttribute(als_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); attr = true; }
+        static std::atomic<unsigned long long> attr{0};
+        TN_CUDA(tn_smem_optin(als_kernel, 200 * 1024, attr));
         if (smem > 200 * 1024) return TN_EINVAL;
         als_kernel<<<c.nl, 256, smem, c.st>>>(aa);
         TN_LAUNCHED();
@@ -1213,8 +1210,8 @@ int recycle_build(Ctx& c, double* F)
     {
         const size_t D2 = (size_t)D * D, nT = 2 * D2 * D2;
         size_t smem = sizeof(double) * (2 * c.nt * nT + 2 * nT + c.nl * D2 + 4 * D2 + 2 * D) + 64;
-        static bool attr = false;
-        if (!attr) { TN_CUDA(cudaFuncSetAttribute(gauge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)); attr = true; }
+        static std::atomic<unsigned long long> attr{0};
+        TN_CUDA(tn_smem_optin(gauge_kernel, 200 * 1024, attr));
         if (smem > 200 * 1024) return TN_EINVAL;
         gauge_kernel<<<1, 256, smem, c.st>>>(ga);
         TN_LAUNCHED();

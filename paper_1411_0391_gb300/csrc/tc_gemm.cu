@@ -391,12 +391,8 @@ template <int KIND>
 int launch_tc(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int Mp, int Np, int nkb, int m, int n,
               double alpha, double beta, double* C, int ldc)
 {
-    static bool attr = false;
-    if (!attr) {
-        TN_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(tc_gemm_kernel<KIND>, (int)SMEM_BYTES, attr));
     dim3 grid(Np / BN, Mp / BM);
     tc_gemm_kernel<KIND><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, Mp, Np, nkb, m, n, alpha, beta, C, ldc);
     TN_LAUNCHED();
