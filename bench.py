@@ -5,18 +5,23 @@ Workload (one "step"): one full-update imaginary-time step of the 2D
 transverse-field Ising model (h = 3.04, tau = 0.005) on the 2-site
 checkerboard iPEPS, D = 4, chi = 64:
   canonical form + iPEPO + simple-update pre-truncation + double layers,
-  a warm-started CTMRG budget of CTM_ITERS iterations (4 directional moves each),
+  a warm-started CTMRG run to convergence (corner spectra change < CTM_TOL,
+  at most CTM_MAX iterations of 4 directional moves),
   bond environments + ALS + assembly of every link type.
-The headline is the precision form (CTMRG contractions as TF32x3 products on
-the tensor cores; projector SVD, bond environment, ALS, gauge fixing in FP64);
-the plain FP64 form and the BF16x3 form are timed on the same steps and
-reported beside it.  The CTMRG budget is fixed so that every implementation
-does the same work per step.  Energy errors: each form's evolved D = 4,
-chi = 64 state against the FP64 form's, and the converged D = 2, chi = 8
-workload against the FP64 oracle.
+The headline is the precision form HEADLINE (the CTMRG contractions on the
+tensor cores; projector SVD, bond environment, ALS, gauge fixing in FP64);
+the plain FP64 form and the other split forms are timed on the same steps
+from the same state and reported beside it.  The measured CTMRG iterations
+per step (k_ctm) are part of the line; the fixed-budget step of earlier
+measurements (FIXED_CTM_ITERS iterations, no convergence test) is a
+secondary field.  Energy errors: each form's CTMRG on the FP64 form's evolved
+state (the environment arithmetic alone), each form's own evolved state
+measured in FP64 (the trajectory), and the D = 2, chi = 8 workload against the
+FP64 oracle.
 
-Prints one JSON line.  --impl reference times the CPU oracle on the same
-workload (a bounded sample, scaled to steps/s).
+Prints one JSON line.  --impl reference times the CPU oracle on a bounded
+sample of the same workload (one prepare, one CTMRG move, one update), scaled
+to a step of REF_MOVES_PER_STEP moves, and says so in the line.
 """
 import argparse
 import json
@@ -32,12 +37,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CTMRG moves/s and ITE steps/s at D=4,χ=64; energy err vs FP64 oracle"
 WL = dict(D=4, chi=64, h=3.04, tau=0.005, cell="checkerboard")
-CTM_ITERS = 4
-MOVES_PER_STEP = 4 * CTM_ITERS
+CTM_TOL, CTM_MAX = 1e-8, 20         # convergence-driven CTMRG per step, warm-started
+FIXED_CTM_ITERS = 4                 # the secondary fixed-budget step
 N_RE = 5                            # recycled steps per environment computation (Sec. VI.C)
-FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (SIMT) at the 2070 MHz boost clock
+HEADLINE = "bf16s4"
+PRECISIONS = {"f64": 0, "tf32x3": 1, "bf16x3": 2, "bf16s4": 3}
+FORMS = ("bf16s4", "f64", "tf32x3", "bf16x3")
+# moves per converged step, for the reference arm's extrapolation: 4 x the warm-started
+# k_ctm the GPU arm measures on this workload (3.0 on GB300, see the bench line's "k_ctm")
+REF_MOVES_PER_STEP = 12
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor rate
-PRECISIONS = {"f64": 0, "tf32x3": 1, "bf16x3": 2}
+FP64_PROBE_ITERS = 4096
 
 
 def parse():
@@ -48,12 +58,14 @@ def parse():
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--profile-moves", type=int, default=0,
                    help="run only this many CTMRG moves and one update at the workload shape (for ncu)")
-    p.add_argument("--profile-precision", default="tf32x3", choices=sorted(PRECISIONS))
+    p.add_argument("--profile-precision", default=HEADLINE, choices=sorted(PRECISIONS))
+    p.add_argument("--profile-steps", type=int, default=0,
+                   help="after a developed environment, run this many converged steps of the headline form (for ncu)")
     p.add_argument("--profile-recycle", type=int, default=0,
                    help="with --profile-moves: after the update, one recycling window of this many steps "
                         "and one simple-update step")
     p.add_argument("--profile-gemm", action="store_true",
-                   help="run only the N x N x N products of the workload (tcgen05 TF32x3 and FP64), 3 launches each")
+                   help="run only the N x N x N products of the workload (tensor-core forms and FP64), 3 launches each")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -116,13 +128,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def oracle_sample():
     """Time the oracle on a bounded sample of one step: prepare, one CTMRG move, update."""
-    import numpy as np
     from oracle import ctmrg as OC
-    from oracle import recycle as OR
     from oracle import fullupdate as OF
     from oracle import canonical as OK
     from oracle import model as OM
-    from paper_1411_0391_gb300.inputs import random_peps
+    from paper_1411_0391_gb300.inputs import random_peps, random_matrix
     cell = OC.checkerboard()
     D, chi = WL["D"], WL["chi"]
     A = random_peps(2, D)
@@ -135,7 +145,6 @@ def oracle_sample():
     t1 = time.perf_counter()
     # a dense environment (seeded values): the cost of a move does not depend on them,
     # but the near-empty start environment would let LAPACK take zero shortcuts
-    from paper_1411_0391_gb300.inputs import random_matrix
     env = OC.init_env(cell, chi, D * D)
     for i, site in enumerate(sorted(env)):
         for j, name in enumerate(sorted(env[site])):
@@ -150,10 +159,12 @@ def oracle_sample():
     OF.assemble(Theta, cell, fu)
     t4 = time.perf_counter()
     t_prep, t_move, t_upd = t1 - t0, t3 - t2, t4 - t3
-    t_step = t_prep + MOVES_PER_STEP * t_move + t_upd
+    t_step = t_prep + REF_MOVES_PER_STEP * t_move + t_upd
     return dict(t_prepare=t_prep, t_move=t_move, t_update=t_upd, t_step=t_step,
-                sample="oracle at D=4 chi=64: one prepare, one CTMRG move (dense env), one bond-env+ALS update, "
-                       "scaled to %d moves per step" % MOVES_PER_STEP)
+                t_sample=(t1 - t0) + (t3 - t2) + (t4 - t3),
+                sample="oracle at D=4 chi=64: one prepare, one CTMRG move (dense env), one bond-env+ALS update; "
+                       "a step extrapolated as prepare + %d moves + update (the converged warm CTMRG of the "
+                       "GPU arm)" % REF_MOVES_PER_STEP)
 
 
 def threads_used():
@@ -170,16 +181,19 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    vals = []
     for _ in range(args.warmup):
         oracle_sample()
     samples = [oracle_sample() for _ in range(max(args.steps, 1))]
     t_step = statistics.median(s["t_step"] for s in samples)
     t_move = statistics.median(s["t_move"] for s in samples)
+    sampled = sum(s["t_sample"] for s in samples)
     value = 1.0 / t_step
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "impl": "reference", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_step, "higher_is_better": True,
+        # each timed sample covers part of a step: "steps" is the number of whole steps the
+        # timed samples add up to (sampled seconds / extrapolated seconds per step)
+        "steps": sampled / t_step, "samples_timed": len(samples), "extrapolated": True,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "moves_per_s": 1.0 / t_move,
         "config": workload_config(1),
@@ -203,33 +217,32 @@ def energy_error_small(L, precision):
     ctx.tn_set_time_step(tau)
     ctx.tn_set_state(A)
     cfg = OR.Config(h=h, tau=tau, D=D, chi=chi, ctm_tol=1e-10, ctm_max=500)
-    ctm_tol = 1e-10 if precision == L.TN_F64 else 1e-8
+    ctm_tol = 1e-10 if precision in (L.TN_F64, L.TN_BF16S4) else 1e-8
     env, Ao = None, A
     for _ in range(3):
         ctx.tn_fu_step(ctm_tol, 500)
         Ao, env, _ = OR.fu_step(Ao, OC.checkerboard(), cfg, env)
     ctx.tn_build_double_layer()
     ctx.tn_reset_env()
-    ctx.tn_ctmrg(1e-12 if precision == L.TN_F64 else 1e-8, 500)
+    ctx.tn_ctmrg(1e-12 if precision in (L.TN_F64, L.TN_BF16S4) else 1e-8, 500)
     g = ctx.tn_measure()
     o = OR.energy(Ao, OC.checkerboard(), cfg, tol=1e-12)
     ctx.close()
     return abs(g["e_site"] - o["e_site"]) / abs(o["e_site"]), g["e_site"], o["e_site"]
 
 
-def time_form(L, torch, dev, stream, precision, state, args, flush):
-    """Warm-up, then args.steps timed plain steps and args.steps recycled windows of one precision form."""
+def time_form(L, torch, dev, stream, precision, state, args, flush, recycled=True, fixed=True):
+    """Warm-up, then args.steps timed converged steps (and optionally args.steps recycled
+    windows and args.steps fixed-budget steps) of one precision form."""
     D, chi = WL["D"], WL["chi"]
     ctx = L.Context(D, chi, device=dev, precision=precision)
     ctx.tn_set_hamiltonian(1.0, WL["h"])
     ctx.tn_set_time_step(WL["tau"])
     ctx.tn_set_state(state)
     for _ in range(args.warmup):
-        ctx.tn_step_prepare()
-        ctx.tn_ctmrg(0.0, CTM_ITERS)
-        ctx.tn_step_update()
+        ctx.tn_fu_step(CTM_TOL, CTM_MAX)
     t_prep = t_ctm = t_upd = 0.0
-    launches = svd_calls = svd_iters = 0
+    launches = svd_calls = svd_iters = ctm_iters = nonconv = 0
     torch.cuda.synchronize()
     for _ in range(args.steps):
         flush.zero_()
@@ -239,51 +252,99 @@ def time_form(L, torch, dev, stream, precision, state, args, flush):
         ev[0].record(stream)
         ctx.tn_step_prepare()
         ev[1].record(stream)
-        rep = ctx.tn_ctmrg(0.0, CTM_ITERS)
+        rep = ctx.tn_ctmrg(CTM_TOL, CTM_MAX)
         ev[2].record(stream)
-        svd_calls += rep["svd_calls"]
-        svd_iters += rep["svd_iterations"]
         ctx.tn_step_update()
         ev[3].record(stream)
         torch.cuda.synchronize()
+        svd_calls += rep["svd_calls"]
+        svd_iters += rep["svd_iterations"]
+        ctm_iters += rep["iterations"]
+        nonconv += 0 if rep["converged"] else 1
         launches += L.tn_launch_count() - l0
         t_prep += ev[0].elapsed_time(ev[1]) / 1e3
         t_ctm += ev[1].elapsed_time(ev[2]) / 1e3
         t_upd += ev[2].elapsed_time(ev[3]) / 1e3
-    # recycled form (Sec. VI.C): one environment computation, then N_RE steps with the renormalised gate
-    t_rec = 0.0
-    F = None
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.tn_step_prepare()
-        ctx.tn_ctmrg(0.0, CTM_ITERS)
-        ctx.tn_step_update()
-        F = ctx.tn_recycle(N_RE)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_rec += e0.elapsed_time(e1) / 1e3
-    total = t_prep + t_ctm + t_upd
-    return ctx, dict(total=total, t_prep=t_prep, t_ctm=t_ctm, t_upd=t_upd, launches=launches,
-                     svd_calls=svd_calls, svd_iters=svd_iters, t_rec=t_rec, fidelity=F)
+    out = dict(total=t_prep + t_ctm + t_upd, t_prep=t_prep, t_ctm=t_ctm, t_upd=t_upd, launches=launches,
+               svd_calls=svd_calls, svd_iters=svd_iters, ctm_iters=ctm_iters, nonconverged=nonconv)
+    if fixed:
+        # the fixed-budget step (FIXED_CTM_ITERS iterations, no convergence test): secondary
+        t_fix = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.tn_step_prepare()
+            ctx.tn_ctmrg(0.0, FIXED_CTM_ITERS)
+            ctx.tn_step_update()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_fix += e0.elapsed_time(e1) / 1e3
+        out["t_fixed"] = t_fix
+    if recycled:
+        # recycled form (Sec. VI.C): one converged environment computation, then N_RE steps
+        # with the renormalised gate
+        t_rec, F = 0.0, None
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.tn_step_prepare()
+            ctx.tn_ctmrg(CTM_TOL, CTM_MAX)
+            ctx.tn_step_update()
+            F = ctx.tn_recycle(N_RE)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_rec += e0.elapsed_time(e1) / 1e3
+        out.update(t_rec=t_rec, fidelity=F)
+    return ctx, out
 
 
 def form_summary(r, steps, world):
-    return {"steps_per_s": world * steps / r["total"], "moves_per_s": world * steps * MOVES_PER_STEP / r["t_ctm"],
-            "time_split_s": {"prepare": r["t_prep"], "ctmrg": r["t_ctm"], "update": r["t_upd"]},
-            "projector_svd": {"calls": r["svd_calls"], "iterations_per_call": r["svd_iters"] / max(r["svd_calls"], 1)},
-            "recycled": {"n_re": N_RE, "steps_per_s": world * steps * N_RE / r["t_rec"],
-                         "speedup_vs_plain": (steps * N_RE / r["t_rec"]) / (steps / r["total"]),
-                         "last_fidelity": r["fidelity"]}}
+    out = {"steps_per_s": world * steps / r["total"],
+           "moves_per_s": world * 4 * r["ctm_iters"] / r["t_ctm"],
+           "k_ctm": r["ctm_iters"] / steps, "nonconverged_steps": r["nonconverged"],
+           "time_split_s": {"prepare": r["t_prep"], "ctmrg": r["t_ctm"], "update": r["t_upd"]},
+           "projector_svd": {"calls": r["svd_calls"], "iterations_per_call": r["svd_iters"] / max(r["svd_calls"], 1)}}
+    if "t_fixed" in r:
+        out["fixed_budget"] = {"ctm_iterations_per_step": FIXED_CTM_ITERS,
+                               "steps_per_s": world * steps / r["t_fixed"]}
+    if "t_rec" in r:
+        out["recycled"] = {"n_re": N_RE, "steps_per_s": world * steps * N_RE / r["t_rec"],
+                           "speedup_vs_plain": (steps * N_RE / r["t_rec"]) / (steps / r["total"]),
+                           "last_fidelity": r["fidelity"]}
+    return out
 
 
-def full_size_energy(ctx, iters):
-    """E_site of the evolved state: fresh double layer, warm CTMRG for `iters` iterations, measure."""
+def converged_energy(L, dev, precision, state, tol=1e-9, cap=80):
+    """E_site of `state`: double layer, CTMRG from the trivial start in `precision`
+    (its FP64 start, then its products), observables in FP64."""
+    ctx = L.Context(WL["D"], WL["chi"], device=dev, precision=precision)
+    ctx.tn_set_hamiltonian(1.0, WL["h"])
+    ctx.tn_set_state(state)
     ctx.tn_build_double_layer()
-    ctx.tn_ctmrg(0.0, iters)
-    return ctx.tn_measure()
+    ctx.tn_reset_env()
+    rep = ctx.tn_ctmrg(tol, cap)
+    m = ctx.tn_measure()
+    ctx.close()
+    return m, rep
+
+
+def fp64_peak(L, torch, stream):
+    """Measured FP64 FMA throughput (TFLOP/s): the probe kernel, median of 5 timed launches."""
+    L.tn_fp64_rate_probe(FP64_PROBE_ITERS, stream)
+    torch.cuda.synchronize()
+    rates = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = L.tn_fp64_rate_probe(FP64_PROBE_ITERS, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rates.append(flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return statistics.median(rates)
 
 
 def kernel_time(torch, stream, fn, reps=10):
@@ -323,13 +384,31 @@ def run_gpu(args):
         A = torch.randn(N, N, dtype=torch.float64, device=dev)
         B = torch.randn(N, N, dtype=torch.float64, device=dev)
         C = torch.empty(N, N, dtype=torch.float64, device=dev)
-        work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_TF32X3, N, N, N), dtype=torch.uint8, device=dev)
-        for _ in range(3):
-            L.tn_gemm_split(L.TN_TF32X3, 0, 0, N, N, N, 1.0, A, N, B, N, 0.0, C, N, work, stream)
+        for prec in (L.TN_TF32X3, L.TN_BF16S4):
+            work = torch.empty(L.tn_gemm_split_workspace_bytes(prec, N, N, N), dtype=torch.uint8, device=dev)
+            for _ in range(3):
+                L.tn_gemm_split(prec, 0, 0, N, N, N, 1.0, A, N, B, N, 0.0, C, N, work, stream)
         for _ in range(3):
             L.tn_gemm_f64(0, 0, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, 0, 1, stream)
         torch.cuda.synchronize()
         print(json.dumps({"profile_gemm": N, "launches": L.tn_launch_count()}))
+        return
+
+    if args.profile_steps:
+        # steady state: two converged steps first (past the FP64 start of the split forms),
+        # then the profiled converged steps; "skip" = launches before them
+        ctx = L.Context(D, chi, device=dev, precision=PRECISIONS[args.profile_precision])
+        ctx.tn_set_hamiltonian(1.0, WL["h"])
+        ctx.tn_set_time_step(WL["tau"])
+        ctx.tn_set_state(state)
+        for _ in range(3):
+            ctx.tn_fu_step(CTM_TOL, CTM_MAX)
+        torch.cuda.synchronize()
+        skip = L.tn_launch_count()
+        reps = [ctx.tn_fu_step(CTM_TOL, CTM_MAX)["ctm_iterations"] for _ in range(args.profile_steps)]
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_steps": args.profile_steps, "precision": args.profile_precision, "skip": skip,
+                          "ctm_iterations": reps, "launches": L.tn_launch_count() - skip}))
         return
 
     if args.profile_moves:
@@ -356,105 +435,125 @@ def run_gpu(args):
         return
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)       # larger than the 129 MB L2
+    fp64_tflops = fp64_peak(L, torch, stream)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     results, ctxs = {}, {}
     with ClockSampler(local) as clk:
-        for name in ("tf32x3", "f64", "bf16x3"):
-            ctxs[name], results[name] = time_form(L, torch, dev, stream, PRECISIONS[name], state, args, flush)
-    head = results["tf32x3"]
+        for name in FORMS:
+            main = name in (HEADLINE, "f64")
+            ctxs[name], results[name] = time_form(L, torch, dev, stream, PRECISIONS[name], state, args, flush,
+                                                  recycled=main, fixed=main)
+    head = results[HEADLINE]
     total, t_ctm = max_over_ranks([head["total"], head["t_ctm"]], dist, dev)
     value = whole_job_rate(world, args.steps, total)
 
     import numpy as np
-    # energy at full size.  (1) The environment's precision alone: the FP64 form's evolved state,
-    # loaded into every form, CTMRG converged (warm) in that form, measured in FP64.
-    # (2) Trajectory: each form's own evolved state after the same steps, same CTMRG budget.
-    energies_traj = {name: full_size_energy(ctxs[name], 8)["e_site"] for name in ctxs}
-    ref_state = [np.ascontiguousarray(a) for a in ctxs["f64"].tn_get_state()]
-    energies = {}
-    for name in ctxs:
-        ctxs[name].tn_set_state(ref_state)
-        ctxs[name].tn_build_double_layer()
-        ctxs[name].tn_ctmrg(1e-9 if name == "f64" else 1e-7, 60)
-        energies[name] = ctxs[name].tn_measure()["e_site"]
-    e_ref = energies["f64"]
-
-    # end to end through the public API with host buffers: H2D of the state, the step, D2H of the result
-    ctx = ctxs["tf32x3"]
+    # end to end through the public API with host buffers: H2D of the state, one converged
+    # step (tn_fu_step), D2H of the result
+    ctx = ctxs[HEADLINE]
     host = [np.ascontiguousarray(a) for a in ctx.tn_get_state()]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.tn_set_state(host)
-        ctx.tn_step_prepare()
-        ctx.tn_ctmrg(0.0, CTM_ITERS)
-        ctx.tn_step_update()
+        ctx.tn_fu_step(CTM_TOL, CTM_MAX)
         host = ctx.tn_get_state()
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
     state_bytes = sum(a.nbytes for a in host)
 
-    # kernels of the N x N products: FP64 SIMT GEMM and the tcgen05 split-precision GEMM
+    # energies at full size.  (1) The environment arithmetic alone: the FP64 form's evolved
+    # state, CTMRG from the trivial start converged in each form, observables in FP64.
+    # (2) Trajectory: each form's own evolved state, CTMRG and observables in FP64.
+    states = {name: [np.ascontiguousarray(a) for a in ctxs[name].tn_get_state()] for name in ctxs}
+    for c in ctxs.values():
+        c.close()
+    env_err, env_e, traj_err = {}, {}, {}
+    e_ref, rep_ref = converged_energy(L, dev, L.TN_F64, states["f64"])
+    env_e["f64"] = e_ref["e_site"]
+    for name in FORMS:
+        if name == "f64":
+            continue
+        m, _ = converged_energy(L, dev, PRECISIONS[name], states["f64"])
+        env_e[name] = m["e_site"]
+        env_err[name] = abs(m["e_site"] - e_ref["e_site"]) / abs(e_ref["e_site"])
+        t, _ = converged_energy(L, dev, L.TN_F64, states[name])
+        traj_err[name] = {"e_site": abs(t["e_site"] - e_ref["e_site"]) / abs(e_ref["e_site"]),
+                          "mx": max(abs(a - b) for a, b in zip(t["mx"], e_ref["mx"])),
+                          "abs_mz": max(abs(abs(a) - abs(b)) for a, b in zip(t["mz"], e_ref["mz"]))}
+
+    # the N x N x N products of the move (R_u, R_d, rho): FP64 SIMT GEMM and the
+    # tensor-core forms, each launched alone at the step's shape
     N = chi * D * D
     A = torch.randn(N, N, dtype=torch.float64, device=dev)
     B = torch.randn(N, N, dtype=torch.float64, device=dev)
     C = torch.empty(N, N, dtype=torch.float64, device=dev)
-    work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_TF32X3, N, N, N), dtype=torch.uint8, device=dev)
     t_dgemm = kernel_time(torch, stream, lambda: L.tn_gemm_f64(0, 0, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, 0, 1,
                                                               stream))
-    t_tc = kernel_time(torch, stream, lambda: L.tn_gemm_split(L.TN_TF32X3, 0, 0, N, N, N, 1.0, A, N, B, N, 0.0, C, N,
-                                                             work, stream))
+    t_tc = {}
+    for name in ("tf32x3", "bf16x3", "bf16s4"):
+        prec = PRECISIONS[name]
+        work = torch.empty(L.tn_gemm_split_workspace_bytes(prec, N, N, N), dtype=torch.uint8, device=dev)
+        t_tc[name] = kernel_time(torch, stream, lambda: L.tn_gemm_split(prec, 0, 0, N, N, N, 1.0, A, N, B, N, 0.0,
+                                                                        C, N, work, stream))
+        del work
     csum = clk.summary()
-    sm_mhz = csum.get("sm_mhz") or 2070.0
-    fp64_peak = FP64_NOMINAL_TFLOPS * sm_mhz / 2070.0
     peaks = measured_peaks()
-    tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    peak_src = "of measured" if "bf16_tflops" in peaks else "of fallback"
 
     if rank != 0:
         return
     fsum = {name: form_summary(results[name], args.steps, world) for name in results}
+    hs = fsum[HEADLINE]
+    method_flop = 2.0 * N ** 3
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3+f64", "data": "synthetic",
-        "moves_per_s": world * args.steps * MOVES_PER_STEP / t_ctm,
-        "time_split_s": fsum["tf32x3"]["time_split_s"],
-        "projector_svd": fsum["tf32x3"]["projector_svd"],
-        "recycled": fsum["tf32x3"]["recycled"],
-        "forms": {"f64": fsum["f64"], "bf16x3": fsum["bf16x3"]},
-        "speedup_vs_f64": {"steps": fsum["tf32x3"]["steps_per_s"] / fsum["f64"]["steps_per_s"],
-                           "moves": fsum["tf32x3"]["moves_per_s"] / fsum["f64"]["moves_per_s"],
-                           "recycled_steps_vs_plain_f64": fsum["tf32x3"]["recycled"]["steps_per_s"]
-                           / fsum["f64"]["steps_per_s"]},
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16-slices+f64", "data": "synthetic",
+        "moves_per_s": world * 4 * head["ctm_iters"] / t_ctm,
+        "k_ctm": hs["k_ctm"], "ctm_tol": CTM_TOL, "ctm_max": CTM_MAX, "nonconverged_steps": hs["nonconverged_steps"],
+        "time_split_s": hs["time_split_s"],
+        "projector_svd": hs["projector_svd"],
+        "recycled": hs["recycled"],
+        "fixed_budget": hs["fixed_budget"],
+        "forms": {name: fsum[name] for name in FORMS if name != HEADLINE},
+        "speedup_vs_f64": {"steps": hs["steps_per_s"] / fsum["f64"]["steps_per_s"],
+                           "moves": hs["moves_per_s"] / fsum["f64"]["moves_per_s"],
+                           "recycled_steps_vs_plain_f64": hs["recycled"]["steps_per_s"] / fsum["f64"]["steps_per_s"]},
         "config": workload_config(world),
         "e2e": {"value": world * args.steps / e2e_t, "unit": "steps/s", "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},
         "gpu_launches": int(head["launches"]),
         "clocks": csum,
-        "roofline": {"bound": "alu", "achieved": 2.0 * N ** 3 / t_dgemm / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": 2.0 * N ** 3 / t_dgemm / 1e12 / fp64_peak, "traffic": None,
-                     "kernel": "dgemm_kernel %dx%dx%d (FP64 SIMT; GB300 has no FP64 tensor path)" % (N, N, N),
-                     "peak_source": "derived: 1.25 TFLOP/s FP64 at 2070 MHz scaled to the median sampled SM clock"},
-        "roofline_tensor": {"bound": "tensor", "kernel": "tc_gemm_kernel TF32x3 %dx%dx%d incl. operand split" % (N, N, N),
-                            "achieved": 3 * 2.0 * N ** 3 / t_tc / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
-                            "frac": 3 * 2.0 * N ** 3 / t_tc / 1e12 / tf32_peak, "traffic": None,
-                            "peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32:BF16 dense ratio), of measured",
-                            "ms": t_tc * 1e3, "f64_dgemm_ms": t_dgemm * 1e3},
-        "energy_err": {"full_size_vs_f64": {name: abs(energies[name] - e_ref) / abs(e_ref) for name in energies
-                                            if name != "f64"},
-                       "full_size_e_site": energies,
-                       "full_size_workload": "D=4 chi=64: the FP64 form's evolved state; CTMRG converged in each form "
-                                             "(warm, tol 1e-9 FP64 / 1e-7 split, cap 60 iterations); observables FP64",
-                       "trajectory_vs_f64": {name: abs(energies_traj[name] - energies_traj["f64"])
-                                             / abs(energies_traj["f64"]) for name in energies_traj if name != "f64"},
-                       "trajectory_workload": "each form's own state after the bench's steps (same schedule from the "
-                                              "same start), 8 warm CTMRG iterations, measured in FP64"},
+        "roofline": {"bound": "tensor", "kernel": "oz_gemm_kernel (BF16 integer slices) %dx%dx%d incl. exponent "
+                                                  "and slice passes, launched alone at the step's shape" % (N, N, N),
+                     "achieved": method_flop / t_tc["bf16s4"] / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": method_flop / t_tc["bf16s4"] / 1e12 / bf16_peak, "traffic": None,
+                     "flop_basis": "method FLOPs 2N^3 of the FP64 product it delivers; the tensor pipe executes "
+                                   "10 slice products (20 N^3)",
+                     "peak_source": "bf16_tflops burst, " + peak_src, "ms": t_tc["bf16s4"] * 1e3},
+        "roofline_fp64": {"bound": "alu", "kernel": "dgemm_kernel %dx%dx%d (FP64 SIMT; GB300 has no FP64 tensor "
+                                                    "path)" % (N, N, N),
+                          "achieved": method_flop / t_dgemm / 1e12, "peak": fp64_tflops, "unit": "TFLOP/s",
+                          "frac": method_flop / t_dgemm / 1e12 / fp64_tflops, "traffic": None,
+                          "peak_source": "measured in this run: tn_fp64_rate_probe (FMA chains in registers, "
+                                         "152x8 blocks), median of 5", "ms": t_dgemm * 1e3},
+        "tensor_products_ms": {name: t * 1e3 for name, t in t_tc.items()},
+        "energy_err": {"full_size_env_vs_f64": env_err, "full_size_e_site": env_e,
+                       "full_size_workload": "D=4 chi=64: the FP64 form's evolved state; CTMRG from the trivial "
+                                             "start converged in each form (tol 1e-9, cap 80; the split forms start "
+                                             "in FP64 by their schedule); observables FP64",
+                       "trajectory_vs_f64": traj_err,
+                       "trajectory_workload": "each form's own state after the bench's converged steps and recycled "
+                                              "windows (same schedule from the same start), CTMRG and observables "
+                                              "in FP64"},
     }
-    for name, prec in (("f64", L.TN_F64), ("tf32x3", L.TN_TF32X3)):
+    for name in ("f64", HEADLINE, "tf32x3"):
         try:
-            err, eg, eo = energy_error_small(L, prec)
+            err, eg, eo = energy_error_small(L, PRECISIONS[name])
             line["energy_err"]["vs_oracle_" + name] = {"rel": err, "e_gpu": eg, "e_oracle": eo,
                                                        "workload": "D=2 chi=8 h=3 tau=0.01, 3 plain steps"}
         except Exception as ex:                                 # reported, never hidden
@@ -468,9 +567,10 @@ def run_gpu(args):
 
 def workload_config(world):
     return dict(workload="ITE full-update step, 2D TFIM h=3.04 tau=0.005, checkerboard iPEPS D=4 chi=64, "
-                         "CTMRG budget %d iterations per step; precision form: CTMRG contractions TF32x3 on "
-                         "tensor cores, projector SVD / bond environment / ALS / gauge fix FP64" % CTM_ITERS,
-                **WL, ctm_iterations_per_step=CTM_ITERS, parallelism="replicas" if world > 1 else "single",
+                         "warm CTMRG converged per step (corner-spectrum change < %g, cap %d iterations); "
+                         "precision form: CTMRG contractions as exact-accumulation BF16 slice products on the "
+                         "tensor cores, projector SVD / bond environment / ALS / gauge fix FP64" % (CTM_TOL, CTM_MAX),
+                **WL, ctm_tol=CTM_TOL, ctm_max=CTM_MAX, parallelism="replicas" if world > 1 else "single",
                 l2="flushed between timed steps (256 MB write)")
 
 

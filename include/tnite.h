@@ -47,6 +47,8 @@ extern "C" {
 #define TN_ESTATE    -6   /* call out of order (e.g. no state set) */
 #define TN_ESCRATCH  -7   /* problem larger than the fixed scratch of tn_truncated_svd_noalloc */
 #define TN_ETIMEOUT  -8   /* a bounded device-side wait expired (tensor-core kernels); results invalid */
+#define TN_EUNSTABLE -9   /* warning from tn_evolve: some recycling windows were judged unstable and
+                             redone as plain steps (results written and usable) */
 
 /* ---- configuration ------------------------------------------------------ */
 #define TN_CELL_CHECKERBOARD 2
@@ -55,6 +57,9 @@ extern "C" {
 #define TN_F64    0   /* every contraction in double */
 #define TN_TF32X3 1   /* split-precision tensor-core products, TF32 head + tail (tn_gemm_split) */
 #define TN_BF16X3 2   /* split-precision tensor-core products, BF16 head + tail (tn_gemm_split) */
+#define TN_BF16S4 3   /* exact-accumulation tensor-core products: 4 BF16 integer slices per operand
+                         (the Ozaki scheme), 10 slice products, FP32 accumulation that is exact
+                         by construction; error < 2^-30 of the row/column scales (tn_gemm_split) */
 
 typedef struct tn_config {
     int D;          /* PEPS bond dimension, 1..8 */
@@ -62,8 +67,8 @@ typedef struct tn_config {
     int cell;       /* TN_CELL_CHECKERBOARD or TN_CELL_SINGLE */
     int precision;  /* arithmetic of the CTMRG contractions (C.T, enlarged
                        corners, half-system and loop products, projector
-                       products, renormalisation): TN_F64, TN_TF32X3 or
-                       TN_BF16X3.  The split forms start in FP64 after
+                       products, renormalisation): TN_F64, TN_TF32X3,
+                       TN_BF16X3 or TN_BF16S4.  The split forms start in FP64 after
                        tn_reset_env and switch once the environment has
                        developed (corner spectra within 1e-4 between
                        iterations, or 32 moves); an environment given by
@@ -158,7 +163,10 @@ int tn_step_prepare(void* ctx, tn_step_report* rep);
  * state becomes A~ = Q Theta P (max-abs normalised).  Requires a prior
  * tn_step_prepare and tn_ctmrg. */
 int tn_step_update(void* ctx, tn_step_report* rep);
-/* Plain full-update step: prepare, CTMRG(ctm_tol, ctm_max), update. */
+/* Plain full-update step: prepare, CTMRG(ctm_tol, ctm_max), update.
+ * tn_step_prepare, tn_step_update, tn_fu_step, tn_su_step and tn_recycle
+ * return TN_ENUMERIC when the state they start from or produce holds a NaN
+ * or Inf (the check runs on the device before and after the step). */
 int tn_fu_step(void* ctx, double ctm_tol, int ctm_max, tn_step_report* rep);
 
 /* One simple-update step (no environment): canonical form, Theta = gA, and
@@ -195,6 +203,11 @@ typedef struct tn_evolve_opts {
                               window (counted in n_steps) */
     double als_tol;        /* ALS stop (relative change of PQ); <= 0: 1e-12 */
     int    als_max;        /* ALS sweep cap; <= 0: 50 */
+    double min_fidelity;   /* instability test of a recycling window (Sec. VI.D, VII): a window
+                              whose gauge-fix fidelity F (Eq. 25) is below it, or whose recycled
+                              steps produce a NaN/Inf, is redone as plain full-update steps and
+                              the window length is halved from then on (at least 1); <= 0
+                              disables the F test (the NaN/Inf test always applies) */
 } tn_evolve_opts;
 
 typedef struct tn_evolve_report {
@@ -206,14 +219,18 @@ typedef struct tn_evolve_report {
     double last_fidelity;  /* F of the last recycling window */
     int    checks;         /* THRESHOLD: bond-environment checks made */
     double last_change;    /* THRESHOLD: the last measured change */
+    int    fallbacks;      /* recycling windows judged unstable and redone as plain steps */
+    int    final_n_re;     /* the window length in force at the end */
 } tn_evolve_report;
 
 /* n_steps imaginary-time steps (Sec. VI.B-C).  The threshold mode is the
  * reading of "the environment recycled until the bond-environment change
  * exceeds eps" (the paper itself uses a fixed N_Re).  The ALS settings stay
  * in force for later tn_fu_step / tn_step_update calls.  TN_EINVAL for an
- * unknown mode, n_re < 1 when recycling, check_every < 1, a NaN eps or a
- * negative warmup_plain. */
+ * unknown mode, n_re < 1 when recycling, check_every < 1, a NaN eps or
+ * min_fidelity, or a negative warmup_plain.  Returns TN_OK, TN_EUNSTABLE
+ * (warning: rep->fallbacks windows were redone without recycling) or an
+ * error; TN_ENUMERIC when a plain step produces a NaN/Inf. */
 int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* opts, tn_evolve_report* rep);
 
 /* ---- observables (Sec. VI.D; row a14) ----------------------------------- */
@@ -267,10 +284,16 @@ int tn_gemm_f64(int transA, int transB, int m, int n, int k, double alpha,
                 const double* dB, int ldb, long long strideB, double beta,
                 double* dC, int ldc, long long strideC, int batch, void* stream);
 /* Split-precision C = alpha op(A) op(B) + beta C on the tensor cores
- * (precision TN_TF32X3 or TN_BF16X3; layout and op() as tn_gemm_f64, no
- * batch).  Each FP64 operand is split into head and tail of the tensor-core
- * type, x = hi + lo, and hi.hi + hi.lo + lo.hi is accumulated in FP32
- * (about 2^-21 relative for TF32, 2^-16 for BF16); C is written in FP64.
+ * (precision TN_TF32X3, TN_BF16X3 or TN_BF16S4; layout and op() as
+ * tn_gemm_f64, no batch).  TN_TF32X3 / TN_BF16X3: each FP64 operand is split
+ * into head and tail of the tensor-core type, x = hi + lo, and
+ * hi.hi + hi.lo + lo.hi is accumulated in FP32 (about 2^-21 relative for
+ * TF32, 2^-16 for BF16).  TN_BF16S4: each row of op(A) and column of op(B)
+ * is scaled by a power of two and cut into four 8-bit integer slices held
+ * exactly in BF16; the ten slice products of the four leading levels are
+ * accumulated exactly (integers below 2^24 in FP32, combined in 64-bit
+ * integers), so the error is that of the dropped slices, < 2^-30 of
+ * max|A_i.| max|B_.j| K.  C is written in FP64.
  * This is the contraction arithmetic of the precision form (the paper itself
  * works in double throughout).  d_workspace (device, 256-byte aligned, caller
  * owned) holds the split operands: at least tn_gemm_split_workspace_bytes().
@@ -280,6 +303,21 @@ size_t tn_gemm_split_workspace_bytes(int precision, int m, int n, int k);
 int tn_gemm_split(int precision, int transA, int transB, int m, int n, int k, double alpha,
                   const double* dA, int lda, const double* dB, int ldb, double beta,
                   double* dC, int ldc, void* d_workspace, size_t workspace_bytes, void* stream);
+/* FP64 throughput probe (no counterpart in the paper): launches, on stream and
+ * without synchronising, one kernel in which every thread of 152 x 8 blocks of
+ * 256 runs 8 independent fused multiply-add chains of `iters` steps in
+ * registers, and returns in *flops the FLOPs it performs (2 per FMA).  Timed
+ * with events around the launch it measures the FP64 pipe's peak, the
+ * denominator for the FP64 kernels' roofline.  TN_EINVAL for iters < 1. */
+int tn_fp64_rate_probe(int iters, double* flops, void* stream);
+/* Self-test of the device-side wait limit of the tensor-core kernels (no
+ * counterpart in the paper): launches one thread that waits, with the same
+ * bounded wait those kernels use, on a barrier nothing ever arrives on.  The
+ * wait gives up after about one second, the kernel records the expiry and
+ * returns, and the call reports TN_ETIMEOUT (the flag is cleared, the stream
+ * and every context stay usable).  Returns TN_OK only if the wait did not
+ * expire, which would mean the limit is broken.  Synchronises the stream. */
+int tn_selftest_wait_timeout(void* stream);
 /* Permute a rank <= 8 tensor: out[i_perm[0]]...[i_perm[r-1]] = in[i_0]..[i_{r-1}],
  * i.e. output axis j is input axis perm[j]; dims are the input dims. */
 int tn_permute_f64(const double* d_in, double* d_out, int rank, const int* dims,
@@ -309,12 +347,17 @@ int tn_truncated_svd(void* ctx, const double* dM, int m, int k, double* dU, doub
  *  - Limits: k <= 96 and k <= m; the (m, k) scratch need must fit the array
  *    (e.g. m <= 1024 with k <= 64 fits; m <= 112 always fits), otherwise
  *    TN_ESCRATCH and nothing is run.
- *  - The first call on a device looks up the array's device address with that
- *    device current; make that first call before any stream capture.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current and caches it for the
+ *    process; make that first call before any stream capture begins.  The
+ *    cache is not reset-safe: after cudaDeviceReset the cached address is
+ *    stale.  Devices with an index of 64 or more are looked up on every call.
  *  - Every call on a device shares the array and leaves its contents behind:
  *    calls that overlap on the GPU (other streams, other threads) race.
  *    Nothing in the array is assumed to start at zero.
- *  - stream: cudaStream_t (NULL = legacy default); the call synchronises it.
+ *  - stream: cudaStream_t (NULL = legacy default).  The call waits on the
+ *    stream between subspace iterations (it reads convergence data on the
+ *    host) and synchronises it before returning.
  *    Returns TN_OK or TN_ENOCONV (subspace iteration cap reached). */
 int tn_truncated_svd_noalloc(const double* dM, int m, int k, double* dU, double* dS,
                              double* dV, const double* warm, void* stream);

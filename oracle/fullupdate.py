@@ -26,6 +26,13 @@ Readings (the figures that define E1..E6 are missing):
   physical legs are traced.  The CTM tensors carry an arbitrary overall sign
   and scale, so N is divided by <g|g> = sum N[a,a,b,b]; then it is symmetrised
   and projected on its positive part.
+* 1-site cell (Sec. VI.B): the paper optimises one pair for each link r, d, l, u
+  of the plaquette and then averages, P_h = (P_r + P_l)/2, Q_h = (Q_r + Q_l)/2
+  (likewise v from d and u).  With the per-link two-site cluster above, built
+  from the CTM tensors directly, the clusters around r and l are the same
+  network in a 1-site cell (every site carries the same tensor and the same
+  environment), so the two pairs coincide and each average equals the single
+  pair per link type that full_update computes.
 * ALS (a9): start from the pre-truncation pair, alternate P and Q solves with an
   eigenvalue pseudo-inverse (relative cutoff 1e-12), stop when the link matrix
   M = P Q changes by less than tol * ||M|| (cap max_iter); then balance the pair

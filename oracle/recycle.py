@@ -129,7 +129,7 @@ def recycle_window(A, cell, cfg, n_re, env=None, g=None):
     Ak = info['A0']
     for _ in range(n_re):
         Ak = recycled_step(Ak, cell, g, K)
-    info.update(F=F, gauge_iters=git, K=K, A1=can1['A'])
+    info.update(F=F, gauge_iters=git, K=K, A1=can1['A'], W=W)
     return Ak, env, info
 
 

@@ -15,10 +15,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _PATH = os.path.join(_HERE, "libtnite.so")
 _LIB = None
 
-TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE, TN_ESCRATCH, TN_ETIMEOUT = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE, TN_ESCRATCH, TN_ETIMEOUT, TN_EUNSTABLE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 TN_CELL_CHECKERBOARD, TN_CELL_SINGLE = 2, 1
-TN_F64, TN_TF32X3, TN_BF16X3 = 0, 1, 2
+TN_F64, TN_TF32X3, TN_BF16X3, TN_BF16S4 = 0, 1, 2, 3
 (TN_T_STATE, TN_T_CANON, TN_T_LAMBDA, TN_T_THETA, TN_T_PRE_P, TN_T_PRE_Q, TN_T_DOUBLE,
  TN_T_BOND_ENV, TN_T_FU_P, TN_T_FU_Q, TN_T_GAUGE_W, TN_T_GATE_K, TN_T_PEPO) = range(13)
 
@@ -43,13 +43,13 @@ TN_RECYCLE_OFF, TN_RECYCLE_FIXED, TN_RECYCLE_THRESHOLD = 0, 1, 2
 class tn_evolve_opts(ctypes.Structure):
     _fields_ = [("recycle", c_int), ("n_re", c_int), ("ctm_tol", c_double), ("ctm_max", c_int),
                 ("recycle_eps", c_double), ("check_every", c_int), ("warmup_plain", c_int),
-                ("als_tol", c_double), ("als_max", c_int)]
+                ("als_tol", c_double), ("als_max", c_int), ("min_fidelity", c_double)]
 
 
 class tn_evolve_report(ctypes.Structure):
     _fields_ = [("steps", c_int), ("env_computations", c_int), ("ctm_iterations", c_int),
                 ("ctm_moves", c_int), ("nonconverged", c_int), ("last_fidelity", c_double),
-                ("checks", c_int), ("last_change", c_double)]
+                ("checks", c_int), ("last_change", c_double), ("fallbacks", c_int), ("final_n_re", c_int)]
 
 
 class tn_observables(ctypes.Structure):
@@ -92,6 +92,8 @@ _SIGS = {
     "tn_gemm_split_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int]),
     "tn_gemm_split": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_void_p, c_int,
                               c_double, c_void_p, c_int, c_void_p, c_size_t, c_void_p]),
+    "tn_selftest_wait_timeout": (c_int, [c_void_p]),
+    "tn_fp64_rate_probe": (c_int, [c_int, POINTER(c_double), c_void_p]),
     "tn_permute_f64": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_int), POINTER(c_int), c_void_p]),
     "tn_svd_small": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "tn_eigh_small": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
@@ -165,6 +167,18 @@ def tn_gemm_split(precision, transA, transB, m, n, k, alpha, A, lda, B, ldb, bet
                                c_void_p(B.data_ptr()), ldb, beta, c_void_p(C.data_ptr()), ldc,
                                c_void_p(work.data_ptr()), work.numel() * work.element_size(), _stream_ptr(stream)),
            "tn_gemm_split")
+
+
+def tn_selftest_wait_timeout(stream=None):
+    """Status of the bounded-wait self-test (TN_ETIMEOUT when the limit works)."""
+    return int(lib().tn_selftest_wait_timeout(_stream_ptr(stream)))
+
+
+def tn_fp64_rate_probe(iters, stream=None):
+    """Launch the FP64 FMA probe (no sync); returns the FLOPs it performs."""
+    f = c_double(0.0)
+    _check(lib().tn_fp64_rate_probe(iters, byref(f), _stream_ptr(stream)), "tn_fp64_rate_probe")
+    return f.value
 
 
 def tn_permute_f64(inp, out, dims, perm, stream=None):
@@ -326,17 +340,22 @@ class Context:
         return F.value
 
     def tn_evolve(self, n_steps, recycle=False, n_re=1, ctm_tol=1e-10, ctm_max=500, recycle_eps=None,
-                  check_every=1, warmup_plain=0, als_tol=1e-12, als_max=50):
+                  check_every=1, warmup_plain=0, als_tol=1e-12, als_max=50, min_fidelity=0.0):
         """recycle: False/True (fixed windows of n_re) or "threshold" (windows of at most n_re,
-        ended when the bond environment drifts by more than recycle_eps)."""
+        ended when the bond environment drifts by more than recycle_eps).  The returned
+        "status" is TN_OK or TN_EUNSTABLE (windows redone without recycling: "fallbacks")."""
         mode = TN_RECYCLE_THRESHOLD if recycle == "threshold" else (TN_RECYCLE_FIXED if recycle else TN_RECYCLE_OFF)
         eps = float("inf") if recycle_eps is None else recycle_eps
-        o = tn_evolve_opts(mode, n_re, ctm_tol, ctm_max, eps, check_every, warmup_plain, als_tol, als_max)
+        o = tn_evolve_opts(mode, n_re, ctm_tol, ctm_max, eps, check_every, warmup_plain, als_tol, als_max,
+                           min_fidelity)
         rep = tn_evolve_report()
-        _check(lib().tn_evolve(self.handle, n_steps, byref(o), byref(rep)), "tn_evolve")
+        s = lib().tn_evolve(self.handle, n_steps, byref(o), byref(rep))
+        if s != TN_EUNSTABLE:
+            _check(s, "tn_evolve")
         return dict(steps=rep.steps, env_computations=rep.env_computations, ctm_iterations=rep.ctm_iterations,
                     ctm_moves=rep.ctm_moves, nonconverged=rep.nonconverged, last_fidelity=rep.last_fidelity,
-                    checks=rep.checks, last_change=rep.last_change)
+                    checks=rep.checks, last_change=rep.last_change, fallbacks=rep.fallbacks,
+                    final_n_re=rep.final_n_re, status=s)
 
     def tn_set_projector_cutoff(self, cut):
         _check(lib().tn_set_projector_cutoff(self.handle, cut), "tn_set_projector_cutoff")

@@ -27,7 +27,7 @@ static bool valid_cfg(const tn_config* cfg)
     if (cfg->D < 1 || cfg->D > 6) return false;
     if (cfg->chi < 1 || cfg->chi > 96) return false;
     if (cfg->cell != TN_CELL_CHECKERBOARD && cfg->cell != TN_CELL_SINGLE) return false;
-    if (cfg->precision != TN_F64 && cfg->precision != TN_TF32X3 && cfg->precision != TN_BF16X3) return false;
+    if (cfg->precision < TN_F64 || cfg->precision > TN_BF16S4) return false;
     return true;
 }
 
@@ -41,7 +41,7 @@ static bool plan(Ctx& c)
     bool ok = true;
     auto take = [&](size_t n) { double* p = ar.take(n); if (!ar.counting && !p) ok = false; return p; };
     for (int t = 0; t < MAXT; ++t) {
-        c.A[t] = take(nA); c.Ac[t] = take(nA); c.A0[t] = take(nA); c.A1[t] = take(nA);
+        c.A[t] = take(nA); c.Ac[t] = take(nA); c.A0[t] = take(nA); c.A1[t] = take(nA); c.Asave[t] = take(nA);
         c.Theta[t] = take(nTh);
         for (int g = 0; g < 4; ++g) { c.cmaps[t][g] = take((size_t)D * D); c.K[t][g] = take((size_t)k * D); }
     }
@@ -163,6 +163,7 @@ const char* tn_strerror(int s)
         case TN_ESTATE: return "call out of order (state, time step or environment missing)";
         case TN_ESCRATCH: return "problem larger than the fixed scratch of the allocation-free entry point";
         case TN_ETIMEOUT: return "a bounded device-side wait expired in a tensor-core kernel";
+        case TN_EUNSTABLE: return "recycling judged unstable in some window; those steps were redone without recycling (results written)";
         default: return "unknown status";
     }
 }
@@ -383,29 +384,83 @@ int tn_recycle(void* ctx, int n_re, double* fidelity)
     return TN_OK;
 }
 
+// Recycling windows can go unstable when the recycled environment no longer
+// fits the state (Sec. VI.D and Sec. VII): a window is judged unstable when the
+// gauge-fix fidelity F of Eq. (25) falls below opts->min_fidelity, or when a
+// recycled step produces a non-finite tensor.  Such a window is redone as plain
+// full-update steps, starting from the plain step the window's environment
+// computation already produced (its result is kept in Asave), and the window
+// length is halved for the rest of the evolution (at least 1).
+static int save_state(Ctx& c)
+{
+    const size_t per = 2 * (size_t)c.D * c.D * c.D * c.D;
+    for (int t = 0; t < c.nt; ++t)
+        TN_CUDA(cudaMemcpyAsync(c.Asave[t], c.A[t], per * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    return TN_OK;
+}
+
+static int restore_state(Ctx& c)
+{
+    const size_t per = 2 * (size_t)c.D * c.D * c.D * c.D;
+    for (int t = 0; t < c.nt; ++t)
+        TN_CUDA(cudaMemcpyAsync(c.A[t], c.Asave[t], per * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    c.have_gate = false;
+    return TN_OK;
+}
+
+static bool window_unstable(double F, const tn_evolve_opts* o)
+{
+    return !std::isfinite(F) || (o->min_fidelity > 0.0 && F < o->min_fidelity);
+}
+
+// One plain full-update step inside tn_evolve (an environment computation).
+static int plain_step(void* ctx, const tn_evolve_opts* o, tn_evolve_report& r)
+{
+    tn_step_report sr{};
+    int s = tn_fu_step(ctx, o->ctm_tol, o->ctm_max, &sr);
+    if (s == TN_ENOCONV) r.nonconverged++;
+    else if (s != TN_OK) return s;
+    r.env_computations++;
+    r.ctm_iterations += sr.ctm_iterations;
+    return TN_OK;
+}
+
 // Recycling with the threshold trigger: a window starts with an environment
 // computation (a plain step; its bond environments N_0 are kept) and continues
 // with recycled steps from A_0; after every check_every steps one warm CTMRG
 // iteration on the current state gives its bond environments N (a8), and the
 // window ends once max_links ||N - N_0||_F / ||N_0||_F > eps, or after n_re steps.
-static int evolve_threshold(Ctx& c, void* ctx, int n_steps, const tn_evolve_opts* o, tn_evolve_report& r)
+static int evolve_threshold(Ctx& c, void* ctx, int n_steps, const tn_evolve_opts* o, tn_evolve_report& r,
+                            int& n_re)
 {
     const int k = c.kD;
     const size_t n4 = (size_t)k * k * k * k;
     int done = 0;
     while (done < n_steps) {
-        tn_step_report sr{};
-        int s = tn_fu_step(ctx, o->ctm_tol, o->ctm_max, &sr);
-        if (s == TN_ENOCONV) r.nonconverged++;
-        else if (s != TN_OK) return s;
-        r.env_computations++;
-        r.ctm_iterations += sr.ctm_iterations;
+        TN_TRY(plain_step(ctx, o, r));
         TN_CUDA(cudaMemcpyAsync(c.N4ref, c.N4[0], sizeof(double) * n4 * c.nl, cudaMemcpyDeviceToDevice, c.st));
+        TN_TRY(save_state(c));                       // the plain step's result
         double F = 0.0;
         TN_TRY(recycle_build(c, &F));
         r.last_fidelity = F;
-        for (int w = 1; done < n_steps && w <= o->n_re; ++w) {
-            TN_TRY(recycle_advance(c, 1));
+        if (window_unstable(F, o)) {                 // keep the plain step, shorten later windows
+            TN_TRY(restore_state(c));
+            ++done;
+            r.fallbacks++;
+            n_re = std::max(1, n_re / 2);
+            continue;
+        }
+        const int start = done;
+        for (int w = 1; done < n_steps && w <= n_re; ++w) {
+            int s = recycle_advance(c, 1);
+            if (s == TN_ENUMERIC) {                  // undo the window: back to its plain step
+                TN_TRY(restore_state(c));
+                done = start + 1;
+                r.fallbacks++;
+                n_re = std::max(1, n_re / 2);
+                break;
+            }
+            TN_TRY(s);
             ++done;
             if (w % o->check_every != 0 || done >= n_steps) continue;
             TN_TRY(step_prepare(c, nullptr));
@@ -433,51 +488,48 @@ int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* o, tn_evolve_report*
     if (o->recycle != TN_RECYCLE_OFF && o->n_re < 1) return TN_EINVAL;
     if (o->recycle == TN_RECYCLE_THRESHOLD && (o->check_every < 1 || o->recycle_eps != o->recycle_eps))
         return TN_EINVAL;
-    if (o->warmup_plain < 0) return TN_EINVAL;
+    if (o->warmup_plain < 0 || o->min_fidelity != o->min_fidelity) return TN_EINVAL;
     Ctx& c = *C(ctx);
     c.als_tol = o->als_tol > 0.0 ? o->als_tol : 1e-12;
     c.als_max = o->als_max > 0 ? o->als_max : 50;
     tn_evolve_report r{};
     long long moves0 = c.ctm_moves;
     int done = 0;
+    int n_re = o->n_re;
     // warm-up: plain steps first (the recycled windows start from an evolved state)
     const int warm = o->recycle == TN_RECYCLE_OFF ? 0 : std::min(o->warmup_plain, n_steps);
-    for (; done < warm; ++done) {
-        tn_step_report sr{};
-        int s = tn_fu_step(ctx, o->ctm_tol, o->ctm_max, &sr);
-        if (s == TN_ENOCONV) r.nonconverged++;
-        else if (s != TN_OK) return s;
-        r.env_computations++;
-        r.ctm_iterations += sr.ctm_iterations;
-    }
+    for (; done < warm; ++done) TN_TRY(plain_step(ctx, o, r));
     if (o->recycle == TN_RECYCLE_THRESHOLD) {
-        TN_TRY(evolve_threshold(c, ctx, n_steps - done, o, r));
+        TN_TRY(evolve_threshold(c, ctx, n_steps - done, o, r, n_re));
         r.steps += done;
-        r.ctm_moves = (int)(c.ctm_moves - moves0);
-        if (rep) *rep = r;
-        return TN_OK;
-    }
-    while (done < n_steps) {
-        tn_step_report sr{};
-        int s = tn_fu_step(ctx, o->ctm_tol, o->ctm_max, &sr);
-        if (s == TN_ENOCONV) r.nonconverged++;
-        else if (s != TN_OK) return s;
-        r.env_computations++;
-        r.ctm_iterations += sr.ctm_iterations;
-        if (o->recycle) {
-            int k = std::min(o->n_re, n_steps - done);
+    } else {
+        while (done < n_steps) {
+            TN_TRY(plain_step(ctx, o, r));
+            if (!o->recycle) { done += 1; continue; }
+            const int k = std::min(n_re, n_steps - done);
+            TN_TRY(save_state(c));                   // the plain step's result
             double F = 0.0;
-            TN_TRY(tn_recycle(ctx, k, &F));
+            TN_TRY(recycle_build(c, &F));
             r.last_fidelity = F;
+            int s = window_unstable(F, o) ? TN_EUNSTABLE : recycle_advance(c, k);
+            if (s == TN_EUNSTABLE || s == TN_ENUMERIC) {
+                // redo the window as plain steps: its first step is the one just computed
+                TN_TRY(restore_state(c));
+                for (int j = 1; j < k; ++j) TN_TRY(plain_step(ctx, o, r));
+                r.fallbacks++;
+                n_re = std::max(1, n_re / 2);
+            } else {
+                TN_TRY(s);
+            }
             done += k;
-        } else {
-            done += 1;
         }
+        r.steps = done;
     }
-    r.steps = done;
     r.ctm_moves = (int)(c.ctm_moves - moves0);
+    r.final_n_re = n_re;
+    TN_CUDA(cudaStreamSynchronize(c.st));
     if (rep) *rep = r;
-    return TN_OK;
+    return r.fallbacks ? TN_EUNSTABLE : TN_OK;
 }
 
 int tn_measure(void* ctx, tn_observables* obs)
@@ -536,21 +588,27 @@ int tn_set_projector_cutoff(void* ctx, double cut)
     return TN_OK;
 }
 
+// tensor-core kind of a split precision form (-1: not a split form)
+static int split_kind(int precision)
+{
+    return precision == TN_TF32X3 ? 0 : precision == TN_BF16X3 ? 1 : precision == TN_BF16S4 ? 2 : -1;
+}
+
 size_t tn_gemm_split_workspace_bytes(int precision, int m, int n, int k)
 {
-    if ((precision != TN_TF32X3 && precision != TN_BF16X3) || m < 1 || n < 1 || k < 1) return 0;
-    return gemm_tc_scratch_bytes(precision == TN_TF32X3 ? 0 : 1, m, n, k);
+    if (split_kind(precision) < 0 || m < 1 || n < 1 || k < 1) return 0;
+    return gemm_tc_scratch_bytes(split_kind(precision), m, n, k);
 }
 
 int tn_gemm_split(int precision, int transA, int transB, int m, int n, int k, double alpha,
                   const double* dA, int lda, const double* dB, int ldb, double beta,
                   double* dC, int ldc, void* d_workspace, size_t workspace_bytes, void* stream)
 {
-    if (precision != TN_TF32X3 && precision != TN_BF16X3) return TN_EINVAL;
+    if (split_kind(precision) < 0) return TN_EINVAL;
     if (m < 1 || n < 1 || k < 1 || !dA || !dB || !dC || !d_workspace) return TN_EINVAL;
     if (lda < (transA ? m : k) || ldb < (transB ? k : n) || ldc < n) return TN_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_workspace) % 256) return TN_EINVAL;
-    const int kind = precision == TN_TF32X3 ? 0 : 1;
+    const int kind = split_kind(precision);
     if (workspace_bytes < gemm_tc_scratch_bytes(kind, m, n, k)) return TN_ENOMEM;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Arena ar;
@@ -559,6 +617,19 @@ int tn_gemm_split(int precision, int transA, int transB, int m, int n, int k, do
     TN_TRY(gemm_tc(st, ar, kind, transA != 0, transB != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc));
     int flag = 0;
     TN_TRY(tc_status(st, &flag));
+    return flag ? TN_ETIMEOUT : TN_OK;
+}
+
+int tn_fp64_rate_probe(int iters, double* flops, void* stream)
+{
+    if (iters < 1 || !flops) return TN_EINVAL;
+    return dfma_probe(reinterpret_cast<cudaStream_t>(stream), iters, flops);
+}
+
+int tn_selftest_wait_timeout(void* stream)
+{
+    int flag = 0;
+    TN_TRY(wait_selftest(reinterpret_cast<cudaStream_t>(stream), &flag));
     return flag ? TN_ETIMEOUT : TN_OK;
 }
 

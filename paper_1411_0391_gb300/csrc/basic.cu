@@ -375,6 +375,34 @@ int hash_fill(cudaStream_t st, double* x, long long n, unsigned long long seed)
     return TN_OK;
 }
 
+// FP64 fused multiply-add throughput probe: every thread runs 8 independent
+// FMA chains of `iters` steps in registers (2 * 8 * iters FLOPs per thread).
+// The chains contract towards b / (1 - a), so they stay finite; the final store
+// is conditional on a value they never reach, which keeps them alive.
+__global__ void __launch_bounds__(256) dfma_probe_kernel(double* out, int iters, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = 1e-3 * (c + 1) + 1e-9 * threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c];
+    if (s == -1.0) out[0] = s;
+}
+
+int dfma_probe(cudaStream_t st, int iters, double* flops)
+{
+    const int blocks = 152 * 8, threads = 256;
+    dfma_probe_kernel<<<blocks, threads, 0, st>>>(nullptr, iters, 0.9999999, 1e-9);
+    TN_LAUNCHED();
+    *flops = 2.0 * 8.0 * (double)iters * (double)threads * (double)blocks;
+    return TN_OK;
+}
+
 // y[i] = a * x[i] + b * y[i]
 __global__ void axpby_kernel(double* y, const double* x, long long n, double a, double b)
 {

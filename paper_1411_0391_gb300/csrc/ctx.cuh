@@ -45,6 +45,7 @@ struct Ctx {
     double* Ac[MAXT];          // weighted canonical form (a11)
     double* A0[MAXT];          // recycling reference
     double* A1[MAXT];          // pre-truncated sites / canonical form of the updated state
+    double* Asave[MAXT];       // the plain-step result of a recycling window (fallback)
     double* lam[MAXL];
     double* cmaps[MAXT][4];    // canonical leg maps of the last canonicalisation (D x D)
     double* g = nullptr;       // iPEPO d*d*16
@@ -85,17 +86,31 @@ struct Ctx {
     std::vector<double> prev_spectra;
 
     int N() const { return chi * leg; }
-    // contraction arithmetic of the CTMRG moves now: -1 FP64, 0 TF32 x3, 1 BF16 x3
+    // contraction arithmetic of the CTMRG moves now: -1 FP64, 0 TF32 x3, 1 BF16 x3,
+    // 2 BF16 integer slices with exact accumulation
     int kind() const
     {
         if (!split_ready) return -1;
-        return cfg.precision == TN_TF32X3 ? 0 : cfg.precision == TN_BF16X3 ? 1 : -1;
+        switch (cfg.precision) {
+            case TN_TF32X3: return 0;
+            case TN_BF16X3: return 1;
+            case TN_BF16S4: return 2;
+            default: return -1;
+        }
     }
     // Ritz residual threshold (relative to s_1) of the FP64 projector SVD: the loop
     // matrix of the precision form is itself known only to the accuracy of its
-    // split products (~1e-7 TF32 x3, ~4e-6 BF16 x3), so resolving it further
-    // than 1e-10 (1e-9) buys nothing
-    double svd_tol() const { return kind() == 0 ? 1e-10 : kind() == 1 ? 1e-9 : 1e-13; }
+    // split products (~1e-7 TF32 x3, ~4e-6 BF16 x3, ~1e-9 BF16 slices), so
+    // resolving it further than 1e-10 (1e-9, 1e-12) buys nothing
+    double svd_tol() const
+    {
+        switch (kind()) {
+            case 0: return 1e-10;
+            case 1: return 1e-9;
+            case 2: return 1e-12;
+            default: return 1e-13;
+        }
+    }
     // inverse-square-root cutoff of the projectors (relative to s_1): singular
     // values of the loop matrix below it are dropped (1e-12 unless overridden)
     double proj_cut() const { return cut_override >= 0.0 ? cut_override : 1e-12; }
@@ -125,5 +140,6 @@ int recycle_advance(Ctx& c, int n_re);
 int bond_envs_psd(Ctx& c);
 int env_change(Ctx& c, double* out);
 int measure(Ctx& c, tn_observables* obs);
+int state_finite(Ctx& c, double* const* T, bool* ok);   // ok = no NaN/Inf in the cell's tensors
 
 }  // namespace tn

@@ -21,6 +21,7 @@ int normalize_maxabs(cudaStream_t st, double* x, long long n, int batch, long lo
 int fill(cudaStream_t st, double* x, long long n, double v);
 int hash_fill(cudaStream_t st, double* x, long long n, unsigned long long seed);
 int axpby(cudaStream_t st, double* y, const double* x, long long n, double a, double b);
+int dfma_probe(cudaStream_t st, int iters, double* flops);   // FP64 FMA rate probe (no sync)
 
 // linalg.cu
 int svd_small(cudaStream_t st, const double* A, int m, int n, int batch, double* U, double* S, double* V);
@@ -47,6 +48,9 @@ size_t gemm_tc_scratch_bytes(int kind, int m, int n, int k);
 int gemm_tc(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,
             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
 int tc_status(cudaStream_t st, int* status);
+// runs a kernel whose bounded wait on an mbarrier expires (nothing arrives on it);
+// *status = the device-side wait flag afterwards (3 when the wait expired)
+int wait_selftest(cudaStream_t st, int* status);
 // C = alpha op(A) op(B) + beta C (no batch) in the contraction arithmetic
 // `kind`: -1 = FP64 SIMT, 0 = TF32 x3 tensor cores, 1 = BF16 x3.
 int gemm_any(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,

@@ -100,8 +100,20 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(const double* __restrict_
     }
     tr = block_sum(tr, red);
     const double shift = c_shift * 1.1102230246251565e-16 * tr;
-    blk_chol_inv(G, n, shift, 1e-26, X, dead, red);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xout[e] = X[e];
+    double dmax = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { G[i * n + i] += shift; dmax = fmax(dmax, G[i * n + i]); }
+    __syncthreads();
+    dmax = warp_max(dmax);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        red[0] = m;
+    }
+    __syncthreads();
+    blk_chol_inv<double>(G, n, 1e-26 * red[0], X, dead);     // X: scratch; the inverse lands in G
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xout[e] = G[e];
 }
 
 static size_t chol_smem(int n) { return sizeof(double) * 2 * (size_t)n * n + sizeof(int) * n + 64; }

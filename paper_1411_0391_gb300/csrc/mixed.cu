@@ -60,53 +60,10 @@ __global__ void __launch_bounds__(256) chol32_whiten_kernel(const double* __rest
     }
     __syncthreads();
     const float thr = 1e-5f;       // a unit diagonal carries FP32 rounding of ~n * 6e-8
-    for (int j = 0; j < n; ++j) {
-        const float piv = R[j * n + j];
-        const bool isdead = !(piv > thr);
-        const float r = isdead ? 1.0f : sqrtf(piv);
-        __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) R[j * n + i] = isdead ? 0.0f : R[j * n + i] / r;
-        if (threadIdx.x == 0) { R[j * n + j] = r; dead[j] = isdead ? 1 : 0; }
-        __syncthreads();
-        const int rem = n - j - 1;
-        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            const int a = j + 1 + e / rem, b = j + 1 + e % rem;
-            if (b < a) continue;
-            R[a * n + b] -= R[j * n + a] * R[j * n + b];
-        }
-        __syncthreads();
-    }
-    // R^{-1} by doubling over diagonal blocks: with the inverses X_AA, X_CC of two
-    // adjacent b x b diagonal blocks known, X_AC = -X_AA R_AC X_CC; every pair of a
-    // level is independent, so a level is two parallel products (log2 n levels)
-    float* Tm = Ri + n * n;        // n*n scratch: R_AC X_CC
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        Ri[e] = (i == j) ? 1.0f / R[e] : 0.0f;
-    }
-    __syncthreads();
-    for (int b = 1; b < n; b *= 2) {
-        // element (i, j) of a pair: i in A = [k, k+b), j in C = [k+b, k+2b), k a multiple of 2b
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int i = e / n, j = e % n, k = (i / (2 * b)) * (2 * b);
-            if (i >= k + b || j < k + b || j >= k + 2 * b) continue;
-            float acc = 0.0f;
-            for (int l = k + b; l <= j; ++l) acc = fmaf(R[i * n + l], Ri[l * n + j], acc);
-            Tm[e] = acc;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int i = e / n, j = e % n, k = (i / (2 * b)) * (2 * b);
-            if (i >= k + b || j < k + b || j >= k + 2 * b) continue;
-            float acc = 0.0f;
-            for (int l = i; l < k + b; ++l) acc = fmaf(Ri[i * n + l], Tm[l * n + j], acc);
-            Ri[e] = -acc;
-        }
-        __syncthreads();
-    }
+    blk_chol_inv<float>(R, n, thr, Ri, dead);   // Ri: scratch; R^{-1} lands in R
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, c = e % n;
-        X[e] = dead[c] ? 0.0 : dsc[i] * (double)Ri[e];
+        X[e] = dead[c] ? 0.0 : dsc[i] * (double)R[e];
     }
 }
 
@@ -151,8 +108,19 @@ __global__ void __launch_bounds__(256) orth_fix_kernel(const double* __restrict_
         }
         return;
     }
-    blk_chol_inv(G, n, 0.0, 1e-26, X, dead, red);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xo[e] = X[e];
+    double dmax = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dmax = fmax(dmax, G[i * n + i]);
+    dmax = warp_max(dmax);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        red[0] = m;
+    }
+    __syncthreads();
+    blk_chol_inv<double>(G, n, 1e-26 * red[0], X, dead);     // X: scratch; the inverse lands in G
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xo[e] = G[e];
 }
 
 size_t chol32_smem(int n) { return sizeof(float) * 3 * (size_t)n * n + 64; }

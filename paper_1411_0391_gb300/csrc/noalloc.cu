@@ -31,21 +31,27 @@ namespace {
 
 // Device address of g_noalloc_scratch, looked up once per device.  In host
 // code the symbol is only a stand-in; kernels need the address returned by
-// cudaGetSymbolAddress with the device current.
+// cudaGetSymbolAddress with the device current.  The per-device slots are
+// atomics (two host threads may make their first call on one device at the
+// same time; both store the same address).  Devices with an index beyond the
+// table look the address up on every call.  The cache is not reset-safe: after
+// cudaDeviceReset on a device its slot holds the address of the old context.
 constexpr int MAX_DEVICES = 64;
-double* g_scratch_addr[MAX_DEVICES] = {nullptr};
+std::atomic<double*> g_scratch_addr[MAX_DEVICES];
 
 int scratch_address(double** out)
 {
     int dev = 0;
     TN_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= MAX_DEVICES) return TN_EINVAL;
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        TN_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_scratch_addr[dev] = static_cast<double*>(p);
+    const bool cached = dev >= 0 && dev < MAX_DEVICES;
+    double* p = cached ? g_scratch_addr[dev].load(std::memory_order_acquire) : nullptr;
+    if (!p) {
+        void* a = nullptr;
+        TN_CUDA(cudaGetSymbolAddress(&a, g_noalloc_scratch));
+        p = static_cast<double*>(a);
+        if (cached) g_scratch_addr[dev].store(p, std::memory_order_release);
     }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return TN_OK;
 }
 

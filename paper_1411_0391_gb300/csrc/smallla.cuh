@@ -191,51 +191,59 @@ static __device__ void blk_sign_fix(double* U, int n_rows, int n_cols, double* V
 // n x n, destroyed.  Pivots below dead_rel * max diagonal mark a column as
 // linearly dependent: its column of X is zero (the orthonormalised basis then
 // has a zero column there).  X: row-major n x n.
-static __device__ void blk_chol_inv(double* G, int n, double shift, double dead_rel, double* X, int* dead, double* red)
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v)
 {
-    double dmax = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) { G[i * n + i] += shift; dmax = fmax(dmax, G[i * n + i]); }
-    dmax = warp_max(dmax);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-        red[0] = m;
-    }
-    __syncthreads();
-    const double thr = dead_rel * red[0];
-    __syncthreads();
-    // right-looking Cholesky in place: row j of G becomes row j of R
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Cholesky G = L L^T of the symmetric n x n matrix in shared memory (row-major,
+// leading dimension n), then X = (L^T)^{-1} = R^{-1} (upper triangular), written
+// over G.  Left-looking (Crout) order: at step j every row i >= j takes the dot
+// product of rows i and j of L over the finished columns (contiguous in shared
+// memory, one warp per row), so a step costs two barriers and no integer
+// division.  The inverse goes through M = L^{-1}, one row per step (row i of M
+// needs rows < i; the threads of a step take one column each and read rows of
+// M contiguously), and X = M^T.  A pivot not above thr marks its column dead:
+// L's column is zero below a unit diagonal and X's column is zero.  M: n x n
+// shared scratch; dead: n ints.
+template <typename T>
+__device__ void blk_chol_inv(T* G, int n, T thr, T* M, int* dead)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < n; ++j) {
-        double piv = G[j * n + j];
-        bool isdead = !(piv > thr) || !(piv > 0.0);
-        double r = isdead ? 1.0 : sqrt(piv);
+        const T* Lj = G + j * n;
+        for (int i = j + warp; i < n; i += nw) {
+            const T* Li = G + i * n;
+            T acc = T(0);
+            for (int k = lane; k < j; k += 32) acc = fma(Li[k], Lj[k], acc);
+            acc = warp_sum_t(acc);
+            if (lane == 0) G[i * n + j] -= acc;
+        }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) G[j * n + i] = isdead ? 0.0 : G[j * n + i] / r;
+        const T piv = G[j * n + j];
+        const bool isdead = !(piv > thr);
+        const T r = isdead ? T(1) : sqrt(piv);
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) G[i * n + j] = isdead ? T(0) : G[i * n + j] / r;
         if (threadIdx.x == 0) { G[j * n + j] = r; dead[j] = isdead ? 1 : 0; }
         __syncthreads();
-        const int rem = n - j - 1;
-        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            int a = j + 1 + e / rem, b = j + 1 + e % rem;
-            if (b < a) continue;
-            G[a * n + b] -= G[j * n + a] * G[j * n + b];
+    }
+    for (int i = 0; i < n; ++i) {
+        const T* Li = G + i * n;
+        const T inv = T(1) / Li[i];
+        for (int c = threadIdx.x; c <= i; c += blockDim.x) {
+            T acc = (c == i) ? T(1) : T(0);
+            for (int l = c; l < i; ++l) acc = fma(-Li[l], M[l * n + c], acc);
+            M[i * n + c] = acc * inv;
         }
         __syncthreads();
     }
-    // X = R^{-1}, one column per thread, back substitution
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        for (int i = 0; i < n; ++i) X[i * n + c] = 0.0;
-        X[c * n + c] = 1.0 / G[c * n + c];
-        for (int i = c - 1; i >= 0; --i) {
-            double acc = 0.0;
-            for (int l = i + 1; l <= c; ++l) acc = fma(G[i * n + l], X[l * n + c], acc);
-            X[i * n + c] = -acc / G[i * n + i];
-        }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, c = e % n;
+        G[e] = (i <= c && !dead[c]) ? M[c * n + i] : T(0);
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) if (dead[e % n]) X[e] = 0.0;
     __syncthreads();
 }
 

@@ -943,6 +943,32 @@ __global__ void expect_kernel(const double* rho1, int nt, const double* rho2, in
 }
 
 // ============================================================================
+// finiteness of the state: flag = 1 if any entry is NaN or Inf
+// ============================================================================
+__global__ void nonfinite_kernel(const double* __restrict__ x, long long n, int* __restrict__ flag)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(x[i])) *flag = 1;       // every writer stores the same value
+}
+
+int state_finite(Ctx& c, double* const* T, bool* ok)
+{
+    int* flag = (int*)(c.dscratch + 48);
+    TN_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c.st));
+    const long long n = 2LL * c.D * c.D * c.D * c.D;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152);
+    for (int t = 0; t < c.nt; ++t) {
+        nonfinite_kernel<<<blocks, 256, 0, c.st>>>(T[t], n, flag);
+        TN_LAUNCHED();
+    }
+    int h = 0;
+    TN_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    TN_CUDA(cudaStreamSynchronize(c.st));
+    *ok = (h == 0);
+    return TN_OK;
+}
+
+// ============================================================================
 // host orchestration
 // ============================================================================
 static int apply_legs(Ctx& c, const double* T, double* out, int t, double* const* P, double* const* Q, int D_in)
@@ -980,6 +1006,9 @@ static int prepare_theta(Ctx& c, int* canon_iters)
 {
     if (!c.have_state) return TN_ESTATE;
     if (!c.have_pepo) return TN_ESTATE;
+    bool ok = true;
+    TN_TRY(state_finite(c, c.A, &ok));
+    if (!ok) return TN_ENUMERIC;
     int it = 0;
     TN_TRY(canonicalize(c, c.A, c.Ac, &it, true));                      // a11
     for (int t = 0; t < c.nt; ++t) TN_TRY(apply_pepo(c, c.Ac[t], c.Theta[t]));   // a1
@@ -1118,7 +1147,9 @@ int su_step(Ctx& c, tn_step_report* rep)
     c.prepared = false;
     c.updated = false;
     if (rep) rep->canon_iters = it;
-    return TN_OK;
+    bool ok = true;
+    TN_TRY(state_finite(c, c.A, &ok));
+    return ok ? TN_OK : TN_ENUMERIC;
 }
 
 // Bond environments of every link type (a8) into c.N4, normalised by <g|g>,
@@ -1182,7 +1213,9 @@ int step_update(Ctx& c, tn_step_report* rep)
     }
     c.updated = true;
     c.prepared = false;
-    return TN_OK;
+    bool ok = true;
+    TN_TRY(state_finite(c, c.A, &ok));
+    return ok ? TN_OK : TN_ENUMERIC;
 }
 
 // Steps (i)-(iii) of the window: A_0, canonical form of A~, gauge fix, leg
@@ -1265,7 +1298,9 @@ int recycle_advance(Ctx& c, int n_re)
             TN_TRY(normalize_maxabs(c.st, c.A[t], 2LL * D * D * D * D, 1, 0));
             c.ar.release(mk);
         }
-    return TN_OK;
+    bool ok = true;
+    TN_TRY(state_finite(c, c.A, &ok));
+    return ok ? TN_OK : TN_ENUMERIC;
 }
 
 int recycle(Ctx& c, int n_re, double* F)

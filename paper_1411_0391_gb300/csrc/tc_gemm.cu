@@ -359,6 +359,236 @@ __global__ void split_kernel(const double* __restrict__ X, int ld, int kcontig, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact-accumulation slices (the Ozaki scheme: Ozaki, Ogita, Oishi, Rump,
+// "Error-free transformations of matrix multiplication by using fast routines
+// of matrix multiplication and its applications", Numer. Algorithms 59, 2012).
+//
+// Row i of op(A) is scaled by 2^-e_i, e_i the binary exponent of its largest
+// |entry| (so every scaled entry lies in (-1, 1)), and cut into OZ_S = 4 slices
+// of 8 bits by rounding to nearest:  A_ik = 2^e_i sum_s a^(s)_ik 2^-8(s+1) + r_ik,
+// a^(0) an integer in [-256, 256], the later a^(s) in [-128, 128] (all exact in
+// BF16, which carries 8 significant bits), |r_ik| <= 2^(e_i - 33); likewise the
+// columns of op(B) with exponents f_j.  The product is
+//     C_ij = 2^(e_i + f_j - 16) sum_L 2^-8L  P_L,   P_L = sum_{s+t=L} a^(s) b^(t)
+// over the levels L = 0..3 (10 slice products).  Every product of two slices
+// is an integer of at most 2^16, and a level's partial sum over one 64-deep
+// K block stays within 64 * (2 * 2^15 + 2 * 2^14) < 2^24 (level 3, the largest):
+// the FP32 tensor-core accumulator holds it exactly, whatever its rounding.  Each
+// block's level sums are read from tensor memory, converted to integers (exact)
+// and combined into one 64-bit integer per element,
+//     Q += P_0 2^24 + P_1 2^16 + P_2 2^8 + P_3,
+// so the only rounding of the whole product is the final conversion of Q to
+// double.  The dropped slices and levels leave, per term of the K sum, less
+// than 4 * 2^-33 of the scale 2^(e_i + f_j) <= 4 max|A_i.| max|B_.j|.
+// ---------------------------------------------------------------------------
+constexpr int OZ_S = 4;                                   // slices per operand
+constexpr int OZ_L = 4;                                   // levels kept (s + t <= 3)
+constexpr int OZ_STAGES = 2;
+constexpr uint32_t OZ_A_BYTES = OZ_S * BM * ROWB, OZ_B_BYTES = OZ_S * BN * ROWB;
+constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;   // 96 KB
+constexpr uint32_t OZ_TMEM_COLS = 2 * OZ_L * BN;               // 2 buffers x 4 levels = 512
+constexpr size_t OZ_SMEM_BYTES = (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+constexpr int OZ_PRODUCER = 8;                                 // warps 0-7 drain tensor memory
+constexpr int OZ_THREADS = 32 * (OZ_PRODUCER + 1);
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               int Mp, int Np, int nkb, int M, int N, const int* __restrict__ ea, const int* __restrict__ fb,
+               double alpha, double beta, double* __restrict__ C, int ldc)
+{
+    constexpr int KEL = 64;                                // bf16 K elements per 128-byte row
+    constexpr uint32_t IDESC = instr_desc<1>(BN);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * OZ_STAGE_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 4);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * OZ_STAGES;
+    const uint32_t tfull0 = empty0 + 8 * OZ_STAGES, tfree0 = tfull0 + 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+    if (warp == OZ_PRODUCER) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(OZ_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(full0 + 8 * s, 1); mbar_init(empty0 + 8 * s, 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(tfull0 + 8 * b, 1); mbar_init(tfree0 + 8 * b, 32 * OZ_PRODUCER); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == OZ_PRODUCER) {
+        if (lane == 0) {
+            auto load = [&](int kb) {
+                const int s = kb % OZ_STAGES;
+                const uint32_t st = sbase + s * OZ_STAGE_BYTES, bar = full0 + 8 * s;
+                mbar_expect_tx(bar, OZ_STAGE_BYTES);
+                for (int q = 0; q < OZ_S; ++q) tma_load_2d(st + q * BM * ROWB, &mapA, kb * KEL, q * Mp + m0, bar);
+                for (int q = 0; q < OZ_S; ++q)
+                    tma_load_2d(st + OZ_A_BYTES + q * BN * ROWB, &mapB, kb * KEL, q * Np + n0, bar);
+            };
+            bool ok = true;
+            int issued = 0, kb = 0;
+            for (; issued < OZ_STAGES && issued < nkb; ++issued) load(issued);
+            for (; kb < nkb; ++kb) {
+                const int s = kb % OZ_STAGES, b = kb & 1;
+                if (kb >= 2 && !mbar_wait(tfree0 + 8 * b, ((kb >> 1) - 1) & 1)) { ok = false; break; }
+                if (!mbar_wait(full0 + 8 * s, (kb / OZ_STAGES) & 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t st = sbase + s * OZ_STAGE_BYTES;
+                const uint32_t tb = tmem + (uint32_t)(b * OZ_L * BN);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {                 // 16 bf16 of K (32 bytes) per product
+                    const unsigned long long o = (unsigned long long)(ks * 2);
+#pragma unroll
+                    for (int L = 0; L < OZ_L; ++L)
+#pragma unroll
+                        for (int sa = 0; sa <= L; ++sa) {
+                            const int sb = L - sa;
+                            const unsigned long long da = smem_desc(st + sa * BM * ROWB) + o;
+                            const unsigned long long db = smem_desc(st + OZ_A_BYTES + sb * BN * ROWB) + o;
+                            tc_mma<1>(tb + (uint32_t)(L * BN), da, db, IDESC, (ks != 0 || sa != 0) ? 1u : 0u);
+                        }
+                }
+                tc_commit(empty0 + 8 * s);
+                tc_commit(tfull0 + 8 * b);
+                if (kb >= 1 && issued < nkb) {                   // refill the stage k-block kb-1 used
+                    const int sp = (kb - 1) % OZ_STAGES;
+                    if (!mbar_wait(empty0 + 8 * sp, ((kb - 1) / OZ_STAGES) & 1)) { ok = false; ++kb; break; }
+                    load(issued);
+                    ++issued;
+                }
+            }
+            if (!ok) {
+                for (int j = kb; j < issued; ++j) mbar_wait(full0 + 8 * (j % OZ_STAGES), (j / OZ_STAGES) & 1);
+                atomicExch(&g_tc_status, 1);
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue warp w: TMEM lanes 32 (w % 4) .. + 31 (the rows of the tile it may read)
+        // and the half (w / 4) of the tile's columns
+        constexpr int HC = BN / 2;
+        const int cbase = (warp >> 2) * HC;
+        long long acc[HC];
+#pragma unroll
+        for (int j = 0; j < HC; ++j) acc[j] = 0;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int b = kb & 1;
+            if (!mbar_wait(tfull0 + 8 * b, (kb >> 1) & 1)) ok = false;
+            ok = __all_sync(0xffffffffu, ok);        // warp-uniform: tcgen05.ld is warp-collective
+            tc_fence_after();
+            const uint32_t tb = tmem + lane_off + (uint32_t)(b * OZ_L * BN + cbase);
+#pragma unroll
+            for (int c0 = 0; c0 < HC; c0 += 16) {
+#pragma unroll
+                for (int L = 0; L < OZ_L; ++L) {
+                    uint32_t p[16];
+                    tmem_ld16(tb + (uint32_t)(L * BN + c0), p);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)    // exact integers below 2^24: exact conversions
+                        acc[c0 + j] += (long long)__float2int_rn(__uint_as_float(p[j])) * (1LL << (24 - 8 * L));
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tfree0 + 8 * b);
+            if (!ok) break;
+        }
+        if (!ok) atomicExch(&g_tc_status, 2);
+        const int row = m0 + (warp & 3) * 32 + lane;
+        if (row < M) {
+            double* crow = C + (size_t)row * ldc;
+            // 2^(e_i + f_j - 16) 2^-24; rows or columns of zeros carry a huge negative
+            // exponent (their acc is 0): clamp it so the sum cannot overflow
+            const int er = max(ea[row], -4000) - 40;
+#pragma unroll
+            for (int j = 0; j < HC; ++j) {
+                const int col = n0 + cbase + j;
+                if (col < N) {
+                    double v = alpha * ldexp((double)acc[j], er + max(fb[col], -4000));
+                    if (beta != 0.0) v += beta * crow[col];
+                    crow[col] = v;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == OZ_PRODUCER)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+}
+
+// Binary exponent of max |entry| of every row r of the logical operand X (R x K,
+// layout as split_kernel): e[r] = the e with max < 2^e (frexp), atomically
+// maximised over tiles; e must start at OZ_EMPTY.  Rows of zeros keep OZ_EMPTY.
+constexpr int OZ_EMPTY = -100000;
+
+__global__ void oz_exponent_kernel(const double* __restrict__ X, int ld, int kcontig, int R, int K, int* __restrict__ e)
+{
+    __shared__ int red[32][33];
+    const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // element (r0 + i, k0 + j) goes to red[i][j]
+    for (int i = ty; i < 32; i += 8) {
+        int r, k;
+        double x;
+        if (kcontig) { r = r0 + i; k = k0 + tx; x = (r < R && k < K) ? X[(size_t)r * ld + k] : 0.0; }
+        else { k = k0 + i; r = r0 + tx; x = (r < R && k < K) ? X[(size_t)k * ld + r] : 0.0; }
+        int ex = OZ_EMPTY;
+        if (x != 0.0) frexp(x, &ex);
+        if (kcontig) red[i][tx] = ex; else red[tx][i] = ex;
+    }
+    __syncthreads();
+    if (ty == 0) {
+        int m = OZ_EMPTY;
+        for (int j = 0; j < 32; ++j) m = max(m, red[tx][j]);
+        if (r0 + tx < R && m > OZ_EMPTY) atomicMax(&e[r0 + tx], m);
+    }
+}
+
+// Slices of the scaled operand: out[(q * Rp + r) * Kp + k] = a^(q)_rk (BF16 integers),
+// zero outside R x K and for rows of zeros.
+__global__ void oz_slice_kernel(const double* __restrict__ X, int ld, int kcontig, int R, int K, int Rp, int Kp,
+                                const int* __restrict__ e, __nv_bfloat16* __restrict__ out)
+{
+    __shared__ double tile[32][33];
+    const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (kcontig) {
+        for (int i = ty; i < 32; i += 8) {
+            const int r = r0 + i, k = k0 + tx;
+            tile[i][tx] = (r < R && k < K) ? X[(size_t)r * ld + k] : 0.0;
+        }
+    } else {
+        for (int i = ty; i < 32; i += 8) {
+            const int k = k0 + i, r = r0 + tx;
+            tile[tx][i] = (r < R && k < K) ? X[(size_t)k * ld + r] : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int r = r0 + i, k = k0 + tx;
+        const int er = (r < R) ? e[r] : OZ_EMPTY;
+        double v = (er > OZ_EMPTY) ? ldexp(tile[i][tx], -er) : 0.0;      // |v| < 1, exact scaling
+        for (int q = 0; q < OZ_S; ++q) {
+            const double t = v * 256.0;                                     // exact
+            const double a = trunc(t);                                      // integer in [-255, 255]
+            v = t - a;                                                      // exact remainder
+            out[((size_t)q * Rp + r) * Kp + k] = __float2bfloat16_rn((float)a);   // exact
+        }
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 int encoder()
@@ -401,24 +631,97 @@ int launch_tc(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int
 
 inline int round_up(int x, int q) { return (x + q - 1) / q * q; }
 
+int launch_oz(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int Mp, int Np, int nkb, int m, int n,
+              const int* ea, const int* fb, double alpha, double beta, double* C, int ldc)
+{
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(oz_gemm_kernel, (int)OZ_SMEM_BYTES, attr));
+    dim3 grid(Np / BN, Mp / BM);
+    oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(ma, mb, Mp, Np, nkb, m, n, ea, fb, alpha, beta, C, ldc);
+    TN_LAUNCHED();
+    return TN_OK;
+}
+
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing
+// arrives on, with the wait the tensor-core kernels use.  The wait expires
+// after WAIT_NS, the kernel records the expiry in g_tc_status (value 3) and
+// returns; no TMA copy or tensor memory is involved.
+__global__ void wait_probe_kernel()
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        const uint32_t a = smem_u32(&bar);
+        mbar_init(a, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait(a, 0)) atomicExch(&g_tc_status, 3);
+    }
+}
+
 }  // namespace
+
+int wait_selftest(cudaStream_t st, int* status)
+{
+    wait_probe_kernel<<<1, 32, 0, st>>>();
+    TN_LAUNCHED();
+    return tc_status(st, status);
+}
 
 int tc_tile_n(int, int) { return BN; }
 
 size_t gemm_tc_scratch_bytes(int kind, int m, int n, int k)
 {
     const int bn = tc_tile_n(m, n);
+    if (kind == 2) {
+        const size_t Mp = round_up(m, BM), Np = round_up(n, bn), Kp = round_up(k, 64);
+        return tn_align256(OZ_S * Mp * Kp * 2) + tn_align256(OZ_S * Np * Kp * 2) + tn_align256(Mp * 4)
+             + tn_align256(Np * 4);
+    }
     const int kq = kind == 0 ? 32 : 64;
     const size_t esz = kind == 0 ? 4 : 2;
     const size_t Mp = round_up(m, BM), Np = round_up(n, bn), Kp = round_up(k, kq);
     return tn_align256(2 * Mp * Kp * esz) + tn_align256(2 * Np * Kp * esz);
 }
 
+// Exact-accumulation product (kind 2): exponents, slices, one tensor-core pass.
+static int gemm_oz(cudaStream_t st, Arena& ar, bool ta, bool tb, int m, int n, int k, double alpha,
+                   const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc)
+{
+    const int bn = tc_tile_n(m, n);
+    const int Mp = round_up(m, BM), Np = round_up(n, bn), Kp = round_up(k, 64);
+    const size_t mark = ar.mark();
+    void* As = ar.take((OZ_S * (size_t)Mp * Kp * 2 + 7) / 8);
+    void* Bs = ar.take((OZ_S * (size_t)Np * Kp * 2 + 7) / 8);
+    int* ea = reinterpret_cast<int*>(ar.take(((size_t)Mp * 4 + 7) / 8));
+    int* fb = reinterpret_cast<int*>(ar.take(((size_t)Np * 4 + 7) / 8));
+    if (!As || !Bs || !ea || !fb) { ar.release(mark); return TN_ENOMEM; }
+    // OZ_EMPTY in every byte pattern is not needed: fill with a large negative int
+    TN_CUDA(cudaMemsetAsync(ea, 0x80, (size_t)Mp * 4, st));       // 0x80808080 < OZ_EMPTY
+    TN_CUDA(cudaMemsetAsync(fb, 0x80, (size_t)Np * 4, st));
+    dim3 blk(32, 8);
+    // A: rows m, K-contiguous unless transposed; B: rows n, K-contiguous only when transposed
+    oz_exponent_kernel<<<dim3(Kp / 32, Mp / 32), blk, 0, st>>>(A, lda, ta ? 0 : 1, m, k, ea);
+    TN_LAUNCHED();
+    oz_exponent_kernel<<<dim3(Kp / 32, Np / 32), blk, 0, st>>>(B, ldb, tb ? 1 : 0, n, k, fb);
+    TN_LAUNCHED();
+    oz_slice_kernel<<<dim3(Kp / 32, Mp / 32), blk, 0, st>>>(A, lda, ta ? 0 : 1, m, k, Mp, Kp, ea, (__nv_bfloat16*)As);
+    TN_LAUNCHED();
+    oz_slice_kernel<<<dim3(Kp / 32, Np / 32), blk, 0, st>>>(B, ldb, tb ? 1 : 0, n, k, Np, Kp, fb, (__nv_bfloat16*)Bs);
+    TN_LAUNCHED();
+    CUtensorMap ma, mb;
+    int s1 = make_map(&ma, 1, As, OZ_S * Mp, Kp, BM);
+    int s2 = make_map(&mb, 1, Bs, OZ_S * Np, Kp, bn);
+    if (s1 != TN_OK || s2 != TN_OK) { ar.release(mark); return TN_ECUDA; }
+    const int s = launch_oz(st, ma, mb, Mp, Np, Kp / 64, m, n, ea, fb, alpha, beta, C, ldc);
+    ar.release(mark);       // stream-ordered: later work on this stream may reuse the buffers
+    return s;
+}
+
 int gemm_tc(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,
             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc)
 {
-    if (m < 1 || n < 1 || k < 1 || (kind != 0 && kind != 1)) return TN_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || kind < 0 || kind > 2) return TN_EINVAL;
     TN_TRY(encoder());
+    if (kind == 2) return gemm_oz(st, ar, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     const int bn = tc_tile_n(m, n);
     const int kq = kind == 0 ? 32 : 64;
     const size_t esz = kind == 0 ? 4 : 2;

@@ -21,7 +21,8 @@ def run_field(h, D, chi, tau, steps, method="fu", n_re=1, ctm_tol=1e-8, ctm_max=
     bond environment drifts by more than recycle_eps) or "su" (simple update).
     tau, steps: one time step and count, or lists for a schedule of stages
     (e.g. tau = [0.01, 0.001], steps = [1000, 1000]).  The measurement converges
-    a fresh CTMRG.
+    a fresh CTMRG.  The returned tau and steps are the caller's own values
+    (scalars stay scalars).
     """
     taus = list(tau) if isinstance(tau, (list, tuple)) else [tau]
     counts = list(steps) if isinstance(steps, (list, tuple)) else [steps]
@@ -52,7 +53,7 @@ def run_field(h, D, chi, tau, steps, method="fu", n_re=1, ctm_tol=1e-8, ctm_max=
         ctx.tn_reset_env()
         crep = ctx.tn_ctmrg(measure_tol, measure_max)
         m = ctx.tn_measure()
-        return dict(h=h, method=method, D=D, chi=chi, tau=taus, steps=counts, n_re=n_re, e_site=m["e_site"],
+        return dict(h=h, method=method, D=D, chi=chi, tau=tau, steps=steps, n_re=n_re, e_site=m["e_site"],
                     mx=sum(m["mx"]) / len(m["mx"]), mz=sum(abs(z) for z in m["mz"]) / len(m["mz"]),
                     env_computations=n_env, ctm_converged=crep["converged"], state=ctx.tn_get_state())
     finally:

@@ -63,10 +63,12 @@ def test_precision_forms_validated_on_host(libpath):
     """Every precision value of tn_config is accepted by the workspace query; others are not."""
     from paper_1411_0391_gb300 import _lib
     L = _lib.lib()
-    for prec in (_lib.TN_F64, _lib.TN_TF32X3, _lib.TN_BF16X3):
+    for prec in (_lib.TN_F64, _lib.TN_TF32X3, _lib.TN_BF16X3, _lib.TN_BF16S4):
         cfg = _lib.tn_config(2, 8, _lib.TN_CELL_CHECKERBOARD, prec)
         assert L.tn_workspace_bytes(ctypes.byref(cfg)) > 0
     bad = _lib.tn_config(2, 8, _lib.TN_CELL_CHECKERBOARD, 7)
+    assert L.tn_workspace_bytes(ctypes.byref(bad)) == 0
+    bad = _lib.tn_config(2, 8, _lib.TN_CELL_CHECKERBOARD, -1)
     assert L.tn_workspace_bytes(ctypes.byref(bad)) == 0
 
 
@@ -107,3 +109,26 @@ def test_new_status_strings(libpath):
     L = _lib.lib()
     assert b"tensor-core" in L.tn_strerror(_lib.TN_ETIMEOUT)
     assert b"allocation-free" in L.tn_strerror(_lib.TN_ESCRATCH)
+
+
+def test_evolve_options_validated_on_host(libpath):
+    """tn_evolve rejects malformed options before it looks at the context (no device call):
+    a NaN fidelity threshold, an unknown mode, a zero window, a NaN trigger."""
+    from paper_1411_0391_gb300 import _lib
+    L = _lib.lib()
+    dummy = ctypes.create_string_buffer(64)        # never dereferenced: validation comes first
+    ctx = ctypes.cast(dummy, ctypes.c_void_p)
+    rep = _lib.tn_evolve_report()
+    nan = float("nan")
+    cases = [
+        _lib.tn_evolve_opts(_lib.TN_RECYCLE_FIXED, 2, 1e-8, 10, 0.0, 1, 0, 1e-12, 50, nan),
+        _lib.tn_evolve_opts(7, 2, 1e-8, 10, 0.0, 1, 0, 1e-12, 50, 0.9),
+        _lib.tn_evolve_opts(_lib.TN_RECYCLE_FIXED, 0, 1e-8, 10, 0.0, 1, 0, 1e-12, 50, 0.9),
+        _lib.tn_evolve_opts(_lib.TN_RECYCLE_THRESHOLD, 2, 1e-8, 10, nan, 1, 0, 1e-12, 50, 0.9),
+        _lib.tn_evolve_opts(_lib.TN_RECYCLE_THRESHOLD, 2, 1e-8, 10, 1e-8, 0, 0, 1e-12, 50, 0.9),
+        _lib.tn_evolve_opts(_lib.TN_RECYCLE_FIXED, 2, 1e-8, 10, 0.0, 1, -1, 1e-12, 50, 0.9),
+    ]
+    for o in cases:
+        assert L.tn_evolve(ctx, 4, ctypes.byref(o), ctypes.byref(rep)) == _lib.TN_EINVAL
+    assert L.tn_evolve(None, 4, ctypes.byref(cases[1]), ctypes.byref(rep)) == _lib.TN_EINVAL
+    assert b"unstable" in L.tn_strerror(_lib.TN_EUNSTABLE)

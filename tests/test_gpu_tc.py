@@ -1,10 +1,20 @@
-"""Split-precision tensor-core GEMM (tcgen05, TF32 x3 and BF16 x3) against FP64 numpy.
+"""Split-precision tensor-core GEMM (tcgen05: TF32 x3, BF16 x3, BF16 integer slices) against FP64 numpy.
 
-Error model of the split product (x = hi + lo, hi.hi + hi.lo + lo.hi accumulated
-in FP32): per product term about u^2 |a||b| with u the unit roundoff of the
-head type (2^-11 TF32, 2^-8 BF16) plus FP32 accumulation, 2^-24 per addition.
-The tests bound the error elementwise by a multiple of (|A| |B|)_ij and in
-relative Frobenius norm.
+Error model of the head/tail split product (x = hi + lo, hi.hi + hi.lo + lo.hi
+accumulated in FP32): per product term about u^2 |a||b| with u the unit
+roundoff of the head type (2^-11 TF32, 2^-8 BF16) plus FP32 accumulation,
+2^-24 per addition.  The tests bound the error elementwise by a multiple of
+(|A| |B|)_ij and in relative Frobenius norm.
+
+The integer-slice form (Ozaki scheme, TN_BF16S4) accumulates exactly; its only
+error is the dropped slices: per term < 4 * 2^-33 of 2^(e_i + f_j) <=
+4 max|A_i.| max|B_.j|, i.e. |C - AB|_ij < 8 * 2^-32 * K * max|A_i.| * max|B_.j|
+(the bound tested below keeps a factor 2.5 above it).  For Gaussian operands the
+per-term errors are independent and unbiased (round-to-nearest slices), so
+relative to |C| ~ sqrt(K) the Frobenius error is about 2^-33 times the ratio of
+the row/column scale to a typical entry (~4 for Gaussian rows): ~1e-9, bounded
+at 1e-8.  On integer operands that the slices hold exactly the product must
+come out exact.
 """
 import numpy as np
 import pytest
@@ -17,7 +27,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 # (relative Frobenius, elementwise vs |A||B|) per precision
-TOL = {L.TN_TF32X3: (2e-6, 2e-5), L.TN_BF16X3: (6e-5, 3e-4)}
+TOL = {L.TN_TF32X3: (2e-6, 2e-5), L.TN_BF16X3: (6e-5, 3e-4), L.TN_BF16S4: (1e-8, 3e-8)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -45,7 +55,7 @@ def _run(prec, ta, tb, m, n, k, alpha=1.0, beta=0.0, inst=0):
     return dC.cpu().numpy(), ref, scale
 
 
-@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3])
+@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3, L.TN_BF16S4])
 @pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_split_gemm_ragged(prec, ta, tb):
     """Several tiles with ragged edges in m, n and k, all transpose cases, beta != 0."""
@@ -55,7 +65,7 @@ def test_split_gemm_ragged(prec, ta, tb):
     assert np.max(np.abs(C - ref) / scale) < elem
 
 
-@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3])
+@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3, L.TN_BF16S4])
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (128, 64, 32), (1024, 1024, 1024), (1024, 80, 1024), (80, 1024, 1024)])
 def test_split_gemm_shapes(prec, m, n, k):
     """Single element, one exact tile, the enlarged-corner size N = chi D^2 = 1024 and skinny panels."""
@@ -78,3 +88,55 @@ def test_split_gemm_repeatable():
     C1, _, _ = _run(L.TN_TF32X3, 0, 1, 300, 260, 500, inst=2)
     C2, _, _ = _run(L.TN_TF32X3, 0, 1, 300, 260, 500, inst=2)
     assert np.array_equal(C1, C2)
+
+
+def _slices_bound(A, Bm, k):
+    """20 * 2^-32 * K * max|A_i.| * max|B_.j| (the dropped-slice bound of the integer-slice form)."""
+    return 20.0 * 2.0 ** -32 * k * np.outer(np.abs(A).max(axis=1), np.abs(Bm).max(axis=0))
+
+
+@pytest.mark.parametrize("m,n,k", [(200, 150, 70), (1024, 1024, 1024), (300, 260, 1000)])
+def test_integer_slices_within_dropped_slice_bound(m, n, k):
+    """Rows and columns of very different scales (the exponents are per row/column)."""
+    rng = np.random.default_rng(m + n + k)
+    A = random_matrix((m, k), instance=40) * 10.0 ** rng.uniform(-6, 6, (m, 1))
+    Bm = random_matrix((k, n), instance=41) * 10.0 ** rng.uniform(-6, 6, (1, n))
+    work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_BF16S4, m, n, k), dtype=torch.uint8, device="cuda")
+    dC = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    L.tn_gemm_split(L.TN_BF16S4, 0, 0, m, n, k, 1.0, _dev(A), k, _dev(Bm), n, 0.0, dC, n, work)
+    err = np.abs(dC.cpu().numpy() - A @ Bm)
+    assert np.all(err <= _slices_bound(A, Bm, k) + 1e-15 * np.abs(A) @ np.abs(Bm))
+
+
+@pytest.mark.parametrize("ta,tb,k", [(0, 0, 1024), (1, 1, 1000), (0, 1, 4096)])
+def test_integer_slices_exact_on_integers(ta, tb, k):
+    """Integer operands in [-255, 255] are held exactly by the slices, so every slice
+    product, every FP32 partial sum (integers below 2^24) and the result are exact:
+    the tensor-core accumulation must not round at all."""
+    m, n = 256, 192
+    rng = np.random.default_rng(k + ta)
+    A = rng.integers(-255, 256, (k, m) if ta else (m, k)).astype(np.float64)
+    Bm = rng.integers(-255, 256, (n, k) if tb else (k, n)).astype(np.float64)
+    work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_BF16S4, m, n, k), dtype=torch.uint8, device="cuda")
+    dC = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    L.tn_gemm_split(L.TN_BF16S4, ta, tb, m, n, k, 1.0, _dev(A), m if ta else k, _dev(Bm), k if tb else n, 0.0,
+                    dC, n, work)
+    opA = A.T if ta else A
+    opB = Bm.T if tb else Bm
+    assert np.array_equal(dC.cpu().numpy(), opA @ opB)      # integer sums below 2^53: numpy is exact too
+
+
+def test_integer_slices_zero_rows_and_columns():
+    m, n, k = 130, 70, 90
+    A = random_matrix((m, k), instance=42)
+    Bm = random_matrix((k, n), instance=43)
+    A[[0, 5, 129]] = 0.0
+    Bm[:, [3, 69]] = 0.0
+    work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_BF16S4, m, n, k), dtype=torch.uint8, device="cuda")
+    dC = torch.full((m, n), 7.0, dtype=torch.float64, device="cuda")
+    L.tn_gemm_split(L.TN_BF16S4, 0, 0, m, n, k, 2.0, _dev(A), k, _dev(Bm), n, 0.5, dC, n, work)
+    ref = 2.0 * A @ Bm + 3.5
+    C = dC.cpu().numpy()
+    np.testing.assert_array_equal(C[[0, 5, 129]], ref[[0, 5, 129]])
+    np.testing.assert_array_equal(C[:, [3, 69]], ref[:, [3, 69]])
+    assert np.abs(C - ref).max() < 1e-8 * np.abs(ref).max()
