@@ -60,6 +60,9 @@ extern "C" {
 #define TN_BF16S4 3   /* exact-accumulation tensor-core products: 4 BF16 integer slices per operand
                          (the Ozaki scheme), 10 slice products, FP32 accumulation that is exact
                          by construction; error < 2^-30 of the row/column scales (tn_gemm_split) */
+#define TN_F64S7  4   /* FP64-accurate tensor-core products: 7 BF16 integer slices per operand,
+                         28 slice products, exact accumulation; error below 2^-54 of the
+                         row/column scales, the unit roundoff of FP64 (tn_gemm_split) */
 
 typedef struct tn_config {
     int D;          /* PEPS bond dimension, 1..8 */
@@ -68,7 +71,10 @@ typedef struct tn_config {
     int precision;  /* arithmetic of the CTMRG contractions (C.T, enlarged
                        corners, half-system and loop products, projector
                        products, renormalisation): TN_F64, TN_TF32X3,
-                       TN_BF16X3 or TN_BF16S4.  The split forms start in FP64 after
+                       TN_BF16X3, TN_BF16S4 or TN_F64S7.  With TN_BF16S4
+                       and TN_F64S7 the products with the loop matrix inside
+                       the projector SVD run as 7-slice (FP64-accurate)
+                       tensor-core products too; TN_F64S7 needs no FP64 start.  The split forms start in FP64 after
                        tn_reset_env and switch once the environment has
                        developed (corner spectra within 1e-4 between
                        iterations, or 32 moves); an environment given by
@@ -293,7 +299,8 @@ int tn_gemm_f64(int transA, int transB, int m, int n, int k, double alpha,
  * exactly in BF16; the ten slice products of the four leading levels are
  * accumulated exactly (integers below 2^24 in FP32, combined in 64-bit
  * integers), so the error is that of the dropped slices, < 2^-30 of
- * max|A_i.| max|B_.j| K.  C is written in FP64.
+ * max|A_i.| max|B_.j| K.  TN_F64S7: the same with seven slices (28
+ * products), error < 2^-54 of max|A_i.| max|B_.j| K.  C is written in FP64.
  * This is the contraction arithmetic of the precision form (the paper itself
  * works in double throughout).  d_workspace (device, 256-byte aligned, caller
  * owned) holds the split operands: at least tn_gemm_split_workspace_bytes().

@@ -34,7 +34,8 @@ Readings (the figures that define E1..E6 are missing):
   environment), so the two pairs coincide and each average equals the single
   pair per link type that full_update computes.
 * ALS (a9): start from the pre-truncation pair, alternate P and Q solves with an
-  eigenvalue pseudo-inverse (relative cutoff 1e-12), stop when the link matrix
+  eigenvalue pseudo-inverse (relative cutoff ALS_PINV_CUTOFF = 1e-12; the paper
+  writes P = R^{-1} S and is silent on the singular case), stop when the link matrix
   M = P Q changes by less than tol * ||M|| (cap max_iter); then balance the pair
   by the SVD of M: P = U sqrt(S), Q = sqrt(S) V^T.  A link whose projected
   environment has no weight (<g|g> = 0)
@@ -45,7 +46,8 @@ import numpy as np
 from .ctmrg import sign_fix, State, rotate_site
 
 LEG = {'l': 1, 'r': 2, 'd': 3, 'u': 4}
-PINV_CUTOFF = 1e-12
+PINV_CUTOFF = 1e-12          # S^{-1/2} of the simple-update pair projectors
+ALS_PINV_CUTOFF = 1e-12      # pseudo-inverse of the ALS normal equations (reading above)
 
 
 def neighbours(cell):
@@ -247,12 +249,13 @@ def psd_project(N4):
     return ((V * w) @ V.T).reshape(N4.shape)
 
 
-def pinv_solve(R, s):
-    """x = R^+ s for symmetric PSD R via its eigenvalues (relative cutoff PINV_CUTOFF)."""
+def pinv_solve(R, s, cutoff=None):
+    """x = R^+ s for symmetric PSD R via its eigenvalues (relative cutoff ALS_PINV_CUTOFF)."""
+    cutoff = ALS_PINV_CUTOFF if cutoff is None else cutoff
     w, V = np.linalg.eigh(0.5 * (R + R.T))
     inv = np.zeros_like(w)
     if w[-1] > 0:
-        keep = w >= PINV_CUTOFF * w[-1]
+        keep = w >= cutoff * w[-1]
         inv[keep] = 1.0 / w[keep]
     return V @ (inv * (V.T @ s))
 

@@ -18,7 +18,7 @@ _LIB = None
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOCONV, TN_ENUMERIC, TN_ESTATE, TN_ESCRATCH, TN_ETIMEOUT, TN_EUNSTABLE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 TN_CELL_CHECKERBOARD, TN_CELL_SINGLE = 2, 1
-TN_F64, TN_TF32X3, TN_BF16X3, TN_BF16S4 = 0, 1, 2, 3
+TN_F64, TN_TF32X3, TN_BF16X3, TN_BF16S4, TN_F64S7 = 0, 1, 2, 3, 4
 (TN_T_STATE, TN_T_CANON, TN_T_LAMBDA, TN_T_THETA, TN_T_PRE_P, TN_T_PRE_Q, TN_T_DOUBLE,
  TN_T_BOND_ENV, TN_T_FU_P, TN_T_FU_Q, TN_T_GAUGE_W, TN_T_GATE_K, TN_T_PEPO) = range(13)
 

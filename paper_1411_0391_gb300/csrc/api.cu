@@ -27,7 +27,7 @@ static bool valid_cfg(const tn_config* cfg)
     if (cfg->D < 1 || cfg->D > 6) return false;
     if (cfg->chi < 1 || cfg->chi > 96) return false;
     if (cfg->cell != TN_CELL_CHECKERBOARD && cfg->cell != TN_CELL_SINGLE) return false;
-    if (cfg->precision < TN_F64 || cfg->precision > TN_BF16S4) return false;
+    if (cfg->precision < TN_F64 || cfg->precision > TN_F64S7) return false;
     return true;
 }
 
@@ -70,8 +70,10 @@ static bool plan(Ctx& c)
     for (int y = 0; y < 4; ++y) { c.Pup[y] = take(N * chi); c.Plo[y] = take(N * chi); }
     c.dscratch = take(64);
     c.scratch_base = ar.mark();
-    // scratch for the largest step (CTMRG cut / bond environment / observables)
-    const size_t scratch = 26 * N * N + 1200 * N + ((size_t)1 << 22);
+    // scratch for the largest step (CTMRG cut / bond environment / observables); the cuts of
+    // a column run concurrently, each on its own share of the scratch
+    const size_t cuts = c.cfg.cell == TN_CELL_CHECKERBOARD ? 2 : 1;
+    const size_t scratch = cuts * (26 * N * N + 1200 * N + ((size_t)1 << 22));
     take(scratch);
     return ok;
 }
@@ -141,6 +143,15 @@ int tn_create(void** out, const tn_config* cfg, void* ws, size_t bytes, void* st
     for (int i = 0; i < c->D; ++i) b[i * c->D + i] = 1.0;
     if (cudaMemcpyAsync(c->boundary, b.data(), sizeof(double) * c->leg, cudaMemcpyHostToDevice, c->st) != cudaSuccess) {
         delete c; return TN_ECUDA;
+    }
+    if (c->Ly > 1) {            // streams and events of the concurrent cuts
+        for (int y = 0; y < c->Ly; ++y) {
+            if (cudaStreamCreateWithFlags(&c->cut_st[y], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&c->ev_join[y], cudaEventDisableTiming) != cudaSuccess) {
+                delete c; return TN_ECUDA;
+            }
+        }
+        if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) { delete c; return TN_ECUDA; }
     }
     int s = ctx_reset_env(*c);
     if (s != TN_OK) { delete c; return s; }
@@ -591,7 +602,13 @@ int tn_set_projector_cutoff(void* ctx, double cut)
 // tensor-core kind of a split precision form (-1: not a split form)
 static int split_kind(int precision)
 {
-    return precision == TN_TF32X3 ? 0 : precision == TN_BF16X3 ? 1 : precision == TN_BF16S4 ? 2 : -1;
+    switch (precision) {
+        case TN_TF32X3: return 0;
+        case TN_BF16X3: return 1;
+        case TN_BF16S4: return 2;
+        case TN_F64S7: return 3;
+        default: return -1;
+    }
 }
 
 size_t tn_gemm_split_workspace_bytes(int precision, int m, int n, int k)

@@ -15,6 +15,7 @@
 // shapes chi x chi and chi x chi x leg; unused directions are zeros.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include "ctx.cuh"
 
 namespace tn {
@@ -114,69 +115,70 @@ static int scale_cols_invsqrt(cudaStream_t st, double* P, int rows, int cols, co
 
 // Enlarged corner of type k at a site: C[k] with edges Ta = T[k] (after) and
 // Tb = T[k-1] (before), as the N x N matrix [(Tb.in, row), (Ta.out, col)].
-static int enlarged_corner(Ctx& c, const Env& e, int k, const double* ab, double* Q)
+static int enlarged_corner(Ctx& c, cudaStream_t st, Arena& ar, const Env& e, int k, const double* ab, double* Q)
 {
     const int chi = c.chi, L = c.leg;
-    size_t mk = c.ar.mark();
-    double* X = c.ar.take((size_t)chi * chi * L);
-    double* Y = c.ar.take((size_t)chi * chi * L * L);
+    size_t mk = ar.mark();
+    double* X = ar.take((size_t)chi * chi * L);
+    double* Y = ar.take((size_t)chi * chi * L * L);
     if (!X || !Y) return TN_ENOMEM;
     const double* C = e.C[k];
     const double* Ta = e.T[k];
     const double* Tb = e.T[(k + 3) & 3];
     const int kd = c.kind();
     // X[o, j, n] = C[o, a] Ta[a, j, n]
-    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, chi, chi * L, chi, 1.0, C, chi, Ta, chi * L, 0.0, X, chi * L));
+    TN_TRY(gemm_any(st, ar, kd, false, false, chi, chi * L, chi, 1.0, C, chi, Ta, chi * L, 0.0, X, chi * L));
     // Y[i, m, j, n] = Tb[i, o, m] X[o, j, n]
-    TN_TRY(contract(c.st, c.ar, "iom,ojn->imjn", dt((double*)Tb, {chi, chi, L}), dt(X, {chi, chi, L}),
+    TN_TRY(contract(st, ar, "iom,ojn->imjn", dt((double*)Tb, {chi, chi, L}), dt(X, {chi, chi, L}),
                     dt(Y, {chi, L, chi, L}), 1.0, 0.0, kd));
     // Q[i, r, j, q] = Y[i, m, j, n] ab[m, n, r, q]
-    TN_TRY(contract(c.st, c.ar, "imjn,mnrq->irjq", dt(Y, {chi, L, chi, L}), dt((double*)ab, {L, L, L, L}),
+    TN_TRY(contract(st, ar, "imjn,mnrq->irjq", dt(Y, {chi, L, chi, L}), dt((double*)ab, {L, L, L, L}),
                     dt(Q, {chi, L, chi, L}), 1.0, 0.0, kd));
-    c.ar.release(mk);
+    ar.release(mk);
     return TN_OK;
 }
 
-// Projectors of the cut (y | y+1) of column x in frame f.
-static int cut_projectors(Ctx& c, Frame& f, int x, int y, double* Pup, double* Plo)
+// Projectors of the cut (y | y+1) of column x in frame f, on stream st with the
+// scratch arena ar (the cuts of a column are independent: each may run on its
+// own stream and arena).  stats: the projector SVD's subspace iterations.
+static int cut_projectors(Ctx& c, Frame& f, int x, int y, double* Pup, double* Plo, cudaStream_t st, Arena& ar,
+                          TsvdStats& stats)
 {
     const int N = c.N(), chi = c.chi;
-    size_t mk = c.ar.mark();
+    size_t mk = ar.mark();
     double* Q[4];
-    for (int k = 0; k < 4; ++k) if (!(Q[k] = c.ar.take((size_t)N * N))) return TN_ENOMEM;
+    for (int k = 0; k < 4; ++k) if (!(Q[k] = ar.take((size_t)N * N))) return TN_ENOMEM;
     const int xs[4] = {x, x + 1, x + 1, x};
     const int ys[4] = {y, y, y + 1, y + 1};
     for (int k = 0; k < 4; ++k) {
         int t = f.tid(xs[k], ys[k]);
-        TN_TRY(enlarged_corner(c, f.e(xs[k], ys[k]), k, c.ab[f.rot][t][k], Q[k]));
+        TN_TRY(enlarged_corner(c, st, ar, f.e(xs[k], ys[k]), k, c.ab[f.rot][t][k], Q[k]));
     }
-    double* Ru = c.ar.take((size_t)N * N);
-    double* Rd = c.ar.take((size_t)N * N);
-    double* rho = c.ar.take((size_t)N * N);
-    double* U = c.ar.take((size_t)N * chi);
-    double* S = c.ar.take(chi);
+    double* Ru = ar.take((size_t)N * N);
+    double* Rd = ar.take((size_t)N * N);
+    double* rho = ar.take((size_t)N * N);
+    double* U = ar.take((size_t)N * chi);
+    double* S = ar.take(chi);
     if (!Ru || !Rd || !rho || !U || !S) return TN_ENOMEM;
     const int kd = c.kind();
-    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, N, N, N, 1.0, Q[0], N, Q[1], N, 0.0, Ru, N));
-    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, N, N, N, 1.0, Q[2], N, Q[3], N, 0.0, Rd, N));
-    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, N, N, N, 1.0, Rd, N, Ru, N, 0.0, rho, N));
+    TN_TRY(gemm_any(st, ar, kd, false, false, N, N, N, 1.0, Q[0], N, Q[1], N, 0.0, Ru, N));
+    TN_TRY(gemm_any(st, ar, kd, false, false, N, N, N, 1.0, Q[2], N, Q[3], N, 0.0, Rd, N));
+    TN_TRY(gemm_any(st, ar, kd, false, false, N, N, N, 1.0, Rd, N, Ru, N, 0.0, rho, N));
     const int xx = ((x % f.Lx) + f.Lx) % f.Lx, yy = ((y % f.Ly) + f.Ly) % f.Ly;
     double* Vw = c.warmV[f.rot][xx][yy];
     // V goes straight into the warm-start slot of this cut
-    TsvdStats stats;
-    // the projector SVD runs in FP64 in every mode (products with rho included)
-    int s = truncated_svd(c.st, c.ar, rho, N, chi, U, S, Vw, c.warm_ok[f.rot][xx][yy] ? Vw : nullptr, &stats,
-                          -1, c.svd_tol());
+    // the projector SVD runs in FP64 in every mode; its products with rho run on the SIMT
+    // pipe or, in the slice forms, as FP64-accurate 7-slice tensor-core products
+    int s = truncated_svd(st, ar, rho, N, chi, U, S, Vw, c.warm_ok[f.rot][xx][yy] ? Vw : nullptr, &stats,
+                          c.svd_kind(), c.svd_tol());
     if (s != TN_OK && s != TN_ENOCONV) return s;
-    c.svd_calls += 1;
-    c.svd_iterations += stats.iterations;
     c.warm_ok[f.rot][xx][yy] = true;
     // P_up = R_d^T U S^{-1/2}, P_lo = R_u V S^{-1/2}
-    TN_TRY(gemm_any(c.st, c.ar, kd, true, false, N, chi, N, 1.0, Rd, N, U, chi, 0.0, Pup, chi));
-    TN_TRY(gemm_any(c.st, c.ar, kd, false, false, N, chi, N, 1.0, Ru, N, Vw, chi, 0.0, Plo, chi));
-    TN_TRY(scale_cols_invsqrt(c.st, Pup, N, chi, S, c.proj_cut()));
-    TN_TRY(scale_cols_invsqrt(c.st, Plo, N, chi, S, c.proj_cut()));
-    c.ar.release(mk);
+    TN_TRY(gemm_any(st, ar, kd, true, false, N, chi, N, 1.0, Rd, N, U, chi, 0.0, Pup, chi));
+    TN_TRY(gemm_any(st, ar, kd, false, false, N, chi, N, 1.0, Ru, N, Vw, chi, 0.0, Plo, chi));
+    TN_TRY(scale_cols_invsqrt(st, Pup, N, chi, S, c.proj_cut()));
+    TN_TRY(scale_cols_invsqrt(st, Plo, N, chi, S, c.proj_cut()));
+    ar.release(mk);
     return TN_OK;
 }
 
@@ -217,11 +219,57 @@ static int renormalize(Ctx& c, Frame& f, int x, int y, const double* pu_above, c
     return TN_OK;
 }
 
+// Projectors of every cut of column x.  The cuts are independent: with more than
+// one, each runs on its own stream (ordered after the context stream by an
+// event, joined back by events) and its own slice of the scratch arena, driven
+// by its own host thread, so that the latency-bound factorisations of the
+// projector SVDs (one SM each) and the host's waits on their convergence tests
+// overlap.
+static int column_projectors(Ctx& c, Frame& f, int x)
+{
+    const int ny = f.Ly;
+    TsvdStats stats[MAXS];
+    if (ny == 1 || !c.cut_st[0]) {
+        for (int y = 0; y < ny; ++y) TN_TRY(cut_projectors(c, f, x, y, c.Pup[y], c.Plo[y], c.st, c.ar, stats[y]));
+    } else {
+        const size_t base = c.ar.mark();
+        const size_t share = ((c.ar.cap - base) / ny) & ~size_t(255);
+        Arena sub[MAXS];
+        for (int y = 0; y < ny; ++y) {
+            sub[y].base = c.ar.base + base + (size_t)y * share;
+            sub[y].cap = share;
+        }
+        TN_CUDA(cudaEventRecord(c.ev_fork, c.st));
+        for (int y = 0; y < ny; ++y) TN_CUDA(cudaStreamWaitEvent(c.cut_st[y], c.ev_fork, 0));
+        int status[MAXS];
+        int dev = 0;
+        TN_CUDA(cudaGetDevice(&dev));
+        std::vector<std::thread> workers;
+        for (int y = 1; y < ny; ++y)
+            workers.emplace_back([&, y]() {
+                cudaSetDevice(dev);
+                status[y] = cut_projectors(c, f, x, y, c.Pup[y], c.Plo[y], c.cut_st[y], sub[y], stats[y]);
+            });
+        status[0] = cut_projectors(c, f, x, 0, c.Pup[0], c.Plo[0], c.cut_st[0], sub[0], stats[0]);
+        for (auto& w : workers) w.join();
+        for (int y = 0; y < ny; ++y) {
+            TN_CUDA(cudaEventRecord(c.ev_join[y], c.cut_st[y]));
+            TN_CUDA(cudaStreamWaitEvent(c.st, c.ev_join[y], 0));
+        }
+        for (int y = 0; y < ny; ++y) TN_TRY(status[y]);
+    }
+    for (int y = 0; y < ny; ++y) {
+        c.svd_calls += 1;
+        c.svd_iterations += stats[y].iterations;
+    }
+    return TN_OK;
+}
+
 int ctmrg_move(Ctx& c, Frame& f)
 {
     const int chi = c.chi, L = c.leg, N = c.N();
     for (int x = 0; x < f.Lx; ++x) {
-        for (int y = 0; y < f.Ly; ++y) TN_TRY(cut_projectors(c, f, x, y, c.Pup[y], c.Plo[y]));
+        TN_TRY(column_projectors(c, f, x));
         size_t mk = c.ar.mark();
         double* nC1[4]; double* nT4[4]; double* nC4[4];
         for (int y = 0; y < f.Ly; ++y) {

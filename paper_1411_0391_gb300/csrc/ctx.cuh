@@ -79,6 +79,18 @@ struct Ctx {
     double* Pup[4];            // projectors of the current column, per y
     double* Plo[4];
     double* dscratch = nullptr;   // small device scratch (reports)
+    // streams and events of the concurrent cuts of a column (created with the context)
+    cudaStream_t cut_st[MAXS] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[MAXS] = {nullptr, nullptr, nullptr, nullptr};
+    ~Ctx()
+    {
+        for (int i = 0; i < MAXS; ++i) {
+            if (cut_st[i]) cudaStreamDestroy(cut_st[i]);
+            if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
     double* hbuf = nullptr;
 
     long long ctm_moves = 0;
@@ -87,9 +99,10 @@ struct Ctx {
 
     int N() const { return chi * leg; }
     // contraction arithmetic of the CTMRG moves now: -1 FP64, 0 TF32 x3, 1 BF16 x3,
-    // 2 BF16 integer slices with exact accumulation
+    // 2 BF16 integer slices (4) with exact accumulation, 3 the same with 7 slices
     int kind() const
     {
+        if (cfg.precision == TN_F64S7) return 3;      // FP64-accurate: no FP64 start needed
         if (!split_ready) return -1;
         switch (cfg.precision) {
             case TN_TF32X3: return 0;
@@ -97,6 +110,12 @@ struct Ctx {
             case TN_BF16S4: return 2;
             default: return -1;
         }
+    }
+    // arithmetic of the products with the loop matrix inside the projector SVD:
+    // FP64 SIMT, or 7-slice FP64-accurate tensor-core products for the slice forms
+    int svd_kind() const
+    {
+        return (cfg.precision == TN_BF16S4 || cfg.precision == TN_F64S7) ? 3 : -1;
     }
     // Ritz residual threshold (relative to s_1) of the FP64 projector SVD: the loop
     // matrix of the precision form is itself known only to the accuracy of its

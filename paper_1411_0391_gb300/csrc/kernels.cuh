@@ -33,6 +33,7 @@ int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols
 int tsvd_columns(int m, int k);
 // mixed.cu: FP32 factorisations refined to FP64 by matrix products
 int orth_mixed(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, int fixes);
+int orth_fixes(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, int fixes);
 int svd_mixed(cudaStream_t st, Arena& ar, const double* B, int n, double* U, double* S, double* V, int steps);
 
 // kind: arithmetic of the products with M (see gemm_any); tol: Ritz residual

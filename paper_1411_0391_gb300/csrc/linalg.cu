@@ -187,9 +187,14 @@ int orth(cudaStream_t st, Arena& ar, double* Y, int rows, int cols)
     return s;
 }
 
-// orth2: columns scaled to unit norm, then Cholesky-QR passes (three with the
-// first shifted, or two plain ones for a basis that is already close to
-// orthogonal up to column scales, as the Ritz panels of the subspace iteration).
+// orth2: columns scaled to unit norm, then Cholesky-QR passes: for an
+// ill-conditioned basis (shifted) a shifted FP64 CholeskyQR, which brings the
+// condition number down to about sqrt(u) kappa, one plain FP64 CholeskyQR,
+// which leaves an orthogonality error of about u kappa(Q_1)^2, and two
+// first-order FP64 corrections, each squaring that error (the last pass of the
+// CholeskyQR3 of Fukaya et al. replaced by products and an O(n^2) kernel); for
+// a basis that is already close to orthogonal up to column scales (the Ritz
+// panels of the subspace iteration) two plain CholeskyQR passes.
 // tmp: rows x cols of caller scratch.
 int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, bool shifted)
 {
@@ -199,14 +204,14 @@ int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols
     if (!G || !X) { ar.release(mk); return TN_ENOMEM; }
     TN_TRY(normalize_cols(st, Y, rows, cols));
     const double c_first = 11.0 * ((double)rows * cols + (double)cols * (cols + 1));
-    const int passes = shifted ? 3 : 2;
-    for (int pass = 0; pass < passes; ++pass) {
+    for (int pass = 0; pass < 2; ++pass) {
         TN_TRY(gemm_splitk(st, ar, true, false, cols, cols, rows, 1.0, Y, cols, Y, cols, 0.0, G, cols));
         TN_TRY(chol_inv(st, G, cols, (shifted && pass == 0) ? c_first : 0.0, X));
         TN_TRY(gemm(st, false, false, rows, cols, cols, 1.0, Y, cols, 0, X, cols, 0, 0.0, tmp, cols, 0, 1));
         TN_CUDA(cudaMemcpyAsync(Y, tmp, sizeof(double) * rows * cols, cudaMemcpyDeviceToDevice, st));
     }
     ar.release(mk);
+    if (shifted) TN_TRY(orth_fixes(st, ar, Y, tmp, rows, cols, 2));
     return TN_OK;
 }
 
@@ -300,8 +305,10 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
         for (int i = 0; i < k; ++i) worst = std::max(worst, hr[i]);
         if (worst <= tol * std::max(hs[0], 1e-300)) { conv = true; break; }
         // a residual that stopped falling may be the FP32 Jacobi's unresolved
-        // near-degenerate pairs: take the exact FP64 Ritz SVD from here on
-        if (!first && worst > 0.5 * prev_worst) exact_rr = true;
+        // near-degenerate pairs: take the exact FP64 Ritz SVD from here on (a
+        // residual that still falls, if slowly, is the subspace iteration's own
+        // rate, which the FP64 Jacobi -- about 20 ms on one SM -- would not help)
+        if (!first && worst > 0.9 * prev_worst) exact_rr = true;
         prev_worst = worst;
     }
     if (it > max_it) it = max_it;

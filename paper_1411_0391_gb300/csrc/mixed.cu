@@ -294,6 +294,29 @@ int orth_mixed(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int
     return TN_OK;
 }
 
+// `fixes` first-order FP64 orthogonality corrections of Y (rows x cols), for a
+// basis already close to orthonormal (each squares the error; the kernel falls
+// back to the FP64 Cholesky inverse where the error is not small).
+int orth_fixes(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols, int fixes)
+{
+    if (cols < 1 || cols > SMALL_MAX) return TN_EINVAL;
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(orth_fix_kernel, (int)orthfix_smem(SMALL_MAX), attr));
+    size_t mk = ar.mark();
+    double* G = ar.take((size_t)cols * cols);
+    double* X = ar.take((size_t)cols * cols);
+    if (!G || !X) { ar.release(mk); return TN_ENOMEM; }
+    for (int pass = 0; pass < fixes; ++pass) {
+        TN_TRY(gemm_splitk(st, ar, true, false, cols, cols, rows, 1.0, Y, cols, Y, cols, 0.0, G, cols));
+        orth_fix_kernel<<<1, 256, orthfix_smem(cols), st>>>(G, cols, X);
+        TN_LAUNCHED();
+        TN_TRY(gemm(st, false, false, rows, cols, cols, 1.0, Y, cols, 0, X, cols, 0, 0.0, tmp, cols, 0, 1));
+        TN_CUDA(cudaMemcpyAsync(Y, tmp, sizeof(double) * rows * cols, cudaMemcpyDeviceToDevice, st));
+    }
+    ar.release(mk);
+    return TN_OK;
+}
+
 // SVD of the n x n row-major B: U, V (n x n row-major, columns = singular
 // vectors, descending), S (n).  FP32 Jacobi, then `steps` FP64 refinement steps.
 int svd_mixed(cudaStream_t st, Arena& ar, const double* B, int n, double* U, double* S, double* V, int steps)

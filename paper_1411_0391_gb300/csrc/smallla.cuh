@@ -200,47 +200,92 @@ __device__ __forceinline__ T warp_sum_t(T v)
 
 // Cholesky G = L L^T of the symmetric n x n matrix in shared memory (row-major,
 // leading dimension n), then X = (L^T)^{-1} = R^{-1} (upper triangular), written
-// over G.  Left-looking (Crout) order: at step j every row i >= j takes the dot
-// product of rows i and j of L over the finished columns (contiguous in shared
-// memory, one warp per row), so a step costs two barriers and no integer
-// division.  The inverse goes through M = L^{-1}, one row per step (row i of M
-// needs rows < i; the threads of a step take one column each and read rows of
-// M contiguously), and X = M^T.  A pivot not above thr marks its column dead:
-// L's column is zero below a unit diagonal and X's column is zero.  M: n x n
-// shared scratch; dead: n ints.
+// over G.  Blocked in panels of CB = 16 columns so that the whole factorisation
+// and inversion take a few dozen block barriers (n = 112: 7 panels), not a few
+// per column -- on one SM the barriers, not the arithmetic, set the time:
+//   panel p: warp 0 factors the panel's columns (rows p.. n-1) with
+//            warp-synchronous steps; then every thread applies the rank-CB
+//            update to the trailing lower triangle (rows and columns >= p + CB);
+//   inverse: M = L^{-1} by block rows: the diagonal blocks' inverses (one warp
+//            per block, forward substitution), then for block row I the blocks
+//            J < I as M_IJ = -M_II sum_{K=J}^{I-1} L_IK M_KJ (two phases);
+//   X = M^T.
+// A pivot not above thr marks its column dead: L's column is zero below a unit
+// diagonal and X's column is zero.  M: n x n shared scratch; dead: n ints.
+constexpr int CB = 16;
+
 template <typename T>
 __device__ void blk_chol_inv(T* G, int n, T thr, T* M, int* dead)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j < n; ++j) {
-        const T* Lj = G + j * n;
-        for (int i = j + warp; i < n; i += nw) {
-            const T* Li = G + i * n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nthr = blockDim.x;
+    for (int p = 0; p < n; p += CB) {
+        const int pe = min(p + CB, n);
+        if (warp == 0) {
+            // unblocked Cholesky of columns p .. pe-1 over rows p .. n-1 (earlier panels'
+            // contributions are already subtracted by their trailing updates)
+            for (int j = p; j < pe; ++j) {
+                T d = G[j * n + j];
+                for (int k = p; k < j; ++k) d -= G[j * n + k] * G[j * n + k];
+                const bool isdead = !(d > thr);
+                const T r = isdead ? T(1) : sqrt(d);
+                for (int i = j + 1 + lane; i < n; i += 32) {
+                    T v = G[i * n + j];
+                    for (int k = p; k < j; ++k) v -= G[i * n + k] * G[j * n + k];
+                    G[i * n + j] = isdead ? T(0) : v / r;
+                }
+                __syncwarp();
+                if (lane == 0) { G[j * n + j] = r; dead[j] = isdead ? 1 : 0; }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // trailing update of the lower triangle: G[i][c] -= sum_{k in panel} L[i][k] L[c][k]
+        const int m = n - pe;
+        for (int e = threadIdx.x; e < m * m; e += nthr) {
+            const int i = pe + e / m, c = pe + e % m;
+            if (c > i) continue;
+            T acc = G[i * n + c];
+            for (int k = p; k < pe; ++k) acc -= G[i * n + k] * G[c * n + k];
+            G[i * n + c] = acc;
+        }
+        __syncthreads();
+    }
+    // M = L^{-1}: diagonal blocks first (one warp each), then block rows
+    const int nb = (n + CB - 1) / CB;
+    const int nw = nthr >> 5;
+    for (int I = warp; I < nb; I += nw) {
+        const int p = I * CB, pe = min(p + CB, n);
+        for (int c = p + lane; c < pe; c += 32) {          // column c of the block's inverse
+            for (int i = p; i < pe; ++i) {
+                T acc = (i == c) ? T(1) : T(0);
+                if (i < c) { M[i * n + c] = T(0); continue; }
+                for (int l = c; l < i; ++l) acc -= G[i * n + l] * M[l * n + c];
+                M[i * n + c] = acc / G[i * n + i];
+            }
+        }
+    }
+    __syncthreads();
+    for (int I = 1; I < nb; ++I) {
+        const int p = I * CB, pe = min(p + CB, n);
+        // phase 1: T_IJ = sum_{K=J}^{I-1} L_IK M_KJ for every J < I, kept in M's upper triangle
+        // (M_IJ itself is written in phase 2; the upper triangle of M is free)
+        for (int e = threadIdx.x; e < (pe - p) * p; e += nthr) {
+            const int i = p + e / p, c = e % p;             // row i of block row I, column c < p
             T acc = T(0);
-            for (int k = lane; k < j; k += 32) acc = fma(Li[k], Lj[k], acc);
-            acc = warp_sum_t(acc);
-            if (lane == 0) G[i * n + j] -= acc;
+            for (int l = c; l < p; ++l) acc += G[i * n + l] * M[l * n + c];
+            M[c * n + i] = acc;                              // transposed slot (c < p <= i): upper triangle
         }
         __syncthreads();
-        const T piv = G[j * n + j];
-        const bool isdead = !(piv > thr);
-        const T r = isdead ? T(1) : sqrt(piv);
-        __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) G[i * n + j] = isdead ? T(0) : G[i * n + j] / r;
-        if (threadIdx.x == 0) { G[j * n + j] = r; dead[j] = isdead ? 1 : 0; }
-        __syncthreads();
-    }
-    for (int i = 0; i < n; ++i) {
-        const T* Li = G + i * n;
-        const T inv = T(1) / Li[i];
-        for (int c = threadIdx.x; c <= i; c += blockDim.x) {
-            T acc = (c == i) ? T(1) : T(0);
-            for (int l = c; l < i; ++l) acc = fma(-Li[l], M[l * n + c], acc);
-            M[i * n + c] = acc * inv;
+        // phase 2: M_IJ = -M_II T_IJ
+        for (int e = threadIdx.x; e < (pe - p) * p; e += nthr) {
+            const int i = p + e / p, c = e % p;
+            T acc = T(0);
+            for (int l = p; l <= i; ++l) acc += M[i * n + l] * M[c * n + l];
+            M[i * n + c] = -acc;
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = threadIdx.x; e < n * n; e += nthr) {
         const int i = e / n, c = e % n;
         G[e] = (i <= c && !dead[c]) ? M[c * n + i] : T(0);
     }

@@ -591,15 +591,17 @@ __global__ void __launch_bounds__(512) psd_kernel(double* N4all, int kD, int* em
 // ============================================================================
 // a9: ALS of Eq. (var1) with a pseudo-inverse, then balancing (one block per link)
 // ============================================================================
+// x = R^+ rhs through the eigenvalues of R; those below cut * max are dropped
+// (the ALS of a9 passes cut = 1e-12)
 __device__ void dev_pinv_solve(const double* R, int n, const double* rhs, double* x, double* A, double* W,
-                               double* w, double* cs, int* pq, double* red, double* tmp)
+                               double* w, double* cs, int* pq, double* red, double* tmp, double cut)
 {
     dev_eigh(R, n, A, w, W, cs, pq, red);
     const double wm = w[n - 1];
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         double acc = 0.0;
         for (int i = 0; i < n; ++i) acc = fma(W[k * n + i], rhs[i], acc);
-        tmp[k] = (wm > 0.0 && w[k] >= 1e-12 * wm) ? acc / w[k] : 0.0;
+        tmp[k] = (wm > 0.0 && w[k] >= cut * wm) ? acc / w[k] : 0.0;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -622,6 +624,7 @@ struct AlsArgs {
     int D;
     double tol;
     int max_iter;
+    double cut;            // relative pseudo-inverse cutoff of the normal equations
 };
 
 __global__ void __launch_bounds__(256) als_kernel(AlsArgs a)
@@ -682,7 +685,7 @@ __global__ void __launch_bounds__(256) als_kernel(AlsArgs a)
             rhs[q] = acc;
         }
         __syncthreads();
-        dev_pinv_solve(R, nR, rhs, P, A, W, w, cs, pq, red, tmp);     // P[(a,i)]
+        dev_pinv_solve(R, nR, rhs, P, A, W, w, cs, pq, red, tmp, a.cut);     // P[(a,i)]
         // Q-step: R[(i,b)][(i',b')] = sum_{a,a'} P[a][i] P[a'][i'] N4[a][b][a'][b']
         for (int q = threadIdx.x; q < nR * nR; q += blockDim.x) {
             int r1 = q / nR, r2 = q % nR;
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(256) als_kernel(AlsArgs a)
             rhs[q] = acc;
         }
         __syncthreads();
-        dev_pinv_solve(R, nR, rhs, Q, A, W, w, cs, pq, red, tmp);     // Q[(i,b)]
+        dev_pinv_solve(R, nR, rhs, Q, A, W, w, cs, pq, red, tmp, a.cut);     // Q[(i,b)]
         dev_mm(P, Q, Mn, k, D, k);
         double dm = 0.0, mn = 0.0;
         for (int q = 0; q < k2; ++q) { double d = Mn[q] - Mo[q]; dm += d * d; mn += Mn[q] * Mn[q]; }
@@ -1190,6 +1193,7 @@ int step_update(Ctx& c, tn_step_report* rep)
     aa.D = c.D;
     aa.tol = c.als_tol;
     aa.max_iter = c.als_max;
+    aa.cut = 1e-12;
     {
         const int nR = k * c.D;
         size_t smem = sizeof(double) * ((size_t)n4 + 3 * (size_t)k * k + 2 * nR + 3 * (size_t)nR * nR + 4 * nR + 2 * (nR / 2 + 1))

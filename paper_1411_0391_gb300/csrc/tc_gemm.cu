@@ -365,7 +365,7 @@ __global__ void split_kernel(const double* __restrict__ X, int ld, int kcontig, 
 // of matrix multiplication and its applications", Numer. Algorithms 59, 2012).
 //
 // Row i of op(A) is scaled by 2^-e_i, e_i the binary exponent of its largest
-// |entry| (so every scaled entry lies in (-1, 1)), and cut into OZ_S = 4 slices
+// |entry| (so every scaled entry lies in (-1, 1)), and cut into S = 4 slices
 // of 8 bits by rounding to nearest:  A_ik = 2^e_i sum_s a^(s)_ik 2^-8(s+1) + r_ik,
 // a^(0) an integer in [-256, 256], the later a^(s) in [-128, 128] (all exact in
 // BF16, which carries 8 significant bits), |r_ik| <= 2^(e_i - 33); likewise the
@@ -382,41 +382,84 @@ __global__ void split_kernel(const double* __restrict__ X, int ld, int kcontig, 
 // double.  The dropped slices and levels leave, per term of the K sum, less
 // than 4 * 2^-33 of the scale 2^(e_i + f_j) <= 4 max|A_i.| max|B_.j|.
 // ---------------------------------------------------------------------------
-constexpr int OZ_S = 4;                                   // slices per operand
-constexpr int OZ_L = 4;                                   // levels kept (s + t <= 3)
-constexpr int OZ_STAGES = 2;
-constexpr uint32_t OZ_A_BYTES = OZ_S * BM * ROWB, OZ_B_BYTES = OZ_S * BN * ROWB;
-constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;   // 96 KB
-constexpr uint32_t OZ_TMEM_COLS = 2 * OZ_L * BN;               // 2 buffers x 4 levels = 512
-constexpr size_t OZ_SMEM_BYTES = (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+// Two configurations: 4 slices (10 products; ~2^-33 of the scales) for the
+// precision form, and 7 slices (28 products; below the FP64 unit roundoff of
+// the scales, 2^-57) for FP64-accurate products.  A K block of KROW elements is
+// one shared-memory row per operand row (128-byte rows with 128-byte swizzle
+// for 4 slices, 64-byte rows with 64-byte swizzle for 7, so that three stages
+// fit); its level sums stay below 2^24 (4 slices: 64 * (2*2^15 + 2*2^14) for
+// level 3; 7 slices: 32 * (2*2^15 + 5*2^14) for level 6) and are drained after
+// every K block.  Levels 0..H-1 are combined into one 64-bit integer and the
+// rest into a second (H = 4 for 4 slices: one integer; H = 3 for 7 slices),
+// each below 2^53 for K <= 2^10 * 64, so both convert to double exactly.
+template <int S> struct OzCfg;
+template <> struct OzCfg<4> {
+    static constexpr int BN = 64, KROW = 64, STAGES = 2, H = 4, SWZ = 2;    // 128-byte swizzle
+};
+template <> struct OzCfg<7> {
+    static constexpr int BN = 32, KROW = 32, STAGES = 3, H = 3, SWZ = 4;    // 64-byte swizzle
+};
 constexpr int OZ_PRODUCER = 8;                                 // warps 0-7 drain tensor memory
 constexpr int OZ_THREADS = 32 * (OZ_PRODUCER + 1);
 
+template <int S>
+struct OzLayout {
+    using C = OzCfg<S>;
+    static constexpr uint32_t ROW = C::KROW * 2;                           // bytes per operand row per stage
+    static constexpr uint32_t A_BYTES = S * BM * ROW, B_BYTES = S * C::BN * ROW;
+    static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t COLS_USED = 2 * S * C::BN;                  // 2 buffers x S levels
+    static constexpr uint32_t TMEM_COLS = COLS_USED <= 256 ? 256 : 512;
+    static constexpr size_t SMEM = (size_t)C::STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+// Shared-memory descriptor of a K-major tile with `swz` swizzle (2: 128-byte rows,
+// 4: 64-byte rows); 8-row groups are 8 rows apart (stride byte offset).
+__device__ __forceinline__ unsigned long long smem_desc_sw(uint32_t saddr, uint32_t row_bytes, uint32_t swz)
+{
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)1 << 16;                              // leading byte offset (ignored)
+    d |= (unsigned long long)((8u * row_bytes) >> 4) << 32;        // stride byte offset
+    d |= (unsigned long long)1 << 46;                              // descriptor version
+    d |= (unsigned long long)swz << 61;
+    return d;
+}
+
+// C (or the partial product of K-split z into P) from the slices; grid
+// (Np / BN, Mp / BM, splits).
+template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                int Mp, int Np, int nkb, int M, int N, const int* __restrict__ ea, const int* __restrict__ fb,
-               double alpha, double beta, double* __restrict__ C, int ldc)
+               double alpha, double beta, double* __restrict__ C, int ldc, double* __restrict__ P)
 {
-    constexpr int KEL = 64;                                // bf16 K elements per 128-byte row
-    constexpr uint32_t IDESC = instr_desc<1>(BN);
+    using Cf = OzCfg<S>;
+    using Ly = OzLayout<S>;
+    constexpr int BNs = Cf::BN, KEL = Cf::KROW, NST = Cf::STAGES, H = Cf::H;
+    constexpr uint32_t IDESC = instr_desc<1>(BNs);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * OZ_STAGE_BYTES);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_STAGES + 4);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NST * Ly::STAGE_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 4);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * OZ_STAGES;
-    const uint32_t tfull0 = empty0 + 8 * OZ_STAGES, tfree0 = tfull0 + 16;
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NST;
+    const uint32_t tfull0 = empty0 + 8 * NST, tfree0 = tfull0 + 16;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNs;
+    // this CTA's K blocks (K split over blockIdx.z)
+    const int kb0 = (int)(((long long)nkb * blockIdx.z) / gridDim.z);
+    const int kb1 = (int)(((long long)nkb * (blockIdx.z + 1)) / gridDim.z);
+    const int nk = kb1 - kb0;
 
     if (warp == OZ_PRODUCER) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(OZ_TMEM_COLS) : "memory");
+                     :: "r"(smem_u32(tslot)), "r"(Ly::TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(full0 + 8 * s, 1); mbar_init(empty0 + 8 * s, 1); }
+        for (int s = 0; s < NST; ++s) { mbar_init(full0 + 8 * s, 1); mbar_init(empty0 + 8 * s, 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(tfull0 + 8 * b, 1); mbar_init(tfree0 + 8 * b, 32 * OZ_PRODUCER); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -427,48 +470,49 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
     if (warp == OZ_PRODUCER) {
         if (lane == 0) {
-            auto load = [&](int kb) {
-                const int s = kb % OZ_STAGES;
-                const uint32_t st = sbase + s * OZ_STAGE_BYTES, bar = full0 + 8 * s;
-                mbar_expect_tx(bar, OZ_STAGE_BYTES);
-                for (int q = 0; q < OZ_S; ++q) tma_load_2d(st + q * BM * ROWB, &mapA, kb * KEL, q * Mp + m0, bar);
-                for (int q = 0; q < OZ_S; ++q)
-                    tma_load_2d(st + OZ_A_BYTES + q * BN * ROWB, &mapB, kb * KEL, q * Np + n0, bar);
+            auto load = [&](int j) {
+                const int s = j % NST;
+                const uint32_t st = sbase + s * Ly::STAGE_BYTES, bar = full0 + 8 * s;
+                mbar_expect_tx(bar, Ly::STAGE_BYTES);
+                for (int q = 0; q < S; ++q) tma_load_2d(st + q * BM * Ly::ROW, &mapA, (kb0 + j) * KEL, q * Mp + m0, bar);
+                for (int q = 0; q < S; ++q)
+                    tma_load_2d(st + Ly::A_BYTES + q * BNs * Ly::ROW, &mapB, (kb0 + j) * KEL, q * Np + n0, bar);
             };
             bool ok = true;
             int issued = 0, kb = 0;
-            for (; issued < OZ_STAGES && issued < nkb; ++issued) load(issued);
-            for (; kb < nkb; ++kb) {
-                const int s = kb % OZ_STAGES, b = kb & 1;
+            for (; issued < NST && issued < nk; ++issued) load(issued);
+            for (; kb < nk; ++kb) {
+                const int s = kb % NST, b = kb & 1;
                 if (kb >= 2 && !mbar_wait(tfree0 + 8 * b, ((kb >> 1) - 1) & 1)) { ok = false; break; }
-                if (!mbar_wait(full0 + 8 * s, (kb / OZ_STAGES) & 1)) { ok = false; break; }
+                if (!mbar_wait(full0 + 8 * s, (kb / NST) & 1)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t st = sbase + s * OZ_STAGE_BYTES;
-                const uint32_t tb = tmem + (uint32_t)(b * OZ_L * BN);
+                const uint32_t st = sbase + s * Ly::STAGE_BYTES;
+                const uint32_t tb = tmem + (uint32_t)(b * S * BNs);
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {                 // 16 bf16 of K (32 bytes) per product
+                for (int ks = 0; ks < KEL / 16; ++ks) {          // 16 bf16 of K (32 bytes) per product
                     const unsigned long long o = (unsigned long long)(ks * 2);
 #pragma unroll
-                    for (int L = 0; L < OZ_L; ++L)
+                    for (int L = 0; L < S; ++L)
 #pragma unroll
                         for (int sa = 0; sa <= L; ++sa) {
                             const int sb = L - sa;
-                            const unsigned long long da = smem_desc(st + sa * BM * ROWB) + o;
-                            const unsigned long long db = smem_desc(st + OZ_A_BYTES + sb * BN * ROWB) + o;
-                            tc_mma<1>(tb + (uint32_t)(L * BN), da, db, IDESC, (ks != 0 || sa != 0) ? 1u : 0u);
+                            const unsigned long long da = smem_desc_sw(st + sa * BM * Ly::ROW, Ly::ROW, Cf::SWZ) + o;
+                            const unsigned long long db =
+                                smem_desc_sw(st + Ly::A_BYTES + sb * BNs * Ly::ROW, Ly::ROW, Cf::SWZ) + o;
+                            tc_mma<1>(tb + (uint32_t)(L * BNs), da, db, IDESC, (ks != 0 || sa != 0) ? 1u : 0u);
                         }
                 }
                 tc_commit(empty0 + 8 * s);
                 tc_commit(tfull0 + 8 * b);
-                if (kb >= 1 && issued < nkb) {                   // refill the stage k-block kb-1 used
-                    const int sp = (kb - 1) % OZ_STAGES;
-                    if (!mbar_wait(empty0 + 8 * sp, ((kb - 1) / OZ_STAGES) & 1)) { ok = false; ++kb; break; }
+                if (kb >= 1 && issued < nk) {                    // refill the stage k-block kb-1 used
+                    const int sp = (kb - 1) % NST;
+                    if (!mbar_wait(empty0 + 8 * sp, ((kb - 1) / NST) & 1)) { ok = false; ++kb; break; }
                     load(issued);
                     ++issued;
                 }
             }
             if (!ok) {
-                for (int j = kb; j < issued; ++j) mbar_wait(full0 + 8 * (j % OZ_STAGES), (j / OZ_STAGES) & 1);
+                for (int j = kb; j < issued; ++j) mbar_wait(full0 + 8 * (j % NST), (j / NST) & 1);
                 atomicExch(&g_tc_status, 1);
             }
         }
@@ -476,28 +520,33 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     } else {
         // epilogue warp w: TMEM lanes 32 (w % 4) .. + 31 (the rows of the tile it may read)
         // and the half (w / 4) of the tile's columns
-        constexpr int HC = BN / 2;
+        constexpr int HC = BNs / 2;
+        constexpr int NACC = (H < S) ? 2 : 1;
         const int cbase = (warp >> 2) * HC;
-        long long acc[HC];
+        long long acc[NACC][HC];
 #pragma unroll
-        for (int j = 0; j < HC; ++j) acc[j] = 0;
+        for (int a = 0; a < NACC; ++a)
+#pragma unroll
+            for (int j = 0; j < HC; ++j) acc[a][j] = 0;
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         bool ok = true;
-        for (int kb = 0; kb < nkb; ++kb) {
+        for (int kb = 0; kb < nk; ++kb) {
             const int b = kb & 1;
             if (!mbar_wait(tfull0 + 8 * b, (kb >> 1) & 1)) ok = false;
             ok = __all_sync(0xffffffffu, ok);        // warp-uniform: tcgen05.ld is warp-collective
             tc_fence_after();
-            const uint32_t tb = tmem + lane_off + (uint32_t)(b * OZ_L * BN + cbase);
+            const uint32_t tb = tmem + lane_off + (uint32_t)(b * S * BNs + cbase);
 #pragma unroll
             for (int c0 = 0; c0 < HC; c0 += 16) {
 #pragma unroll
-                for (int L = 0; L < OZ_L; ++L) {
+                for (int L = 0; L < S; ++L) {
                     uint32_t p[16];
-                    tmem_ld16(tb + (uint32_t)(L * BN + c0), p);
+                    tmem_ld16(tb + (uint32_t)(L * BNs + c0), p);
+                    const int a = L < H ? 0 : 1;
+                    const int sh = L < H ? 8 * (H - 1 - L) : 8 * (S - 1 - L);
 #pragma unroll
                     for (int j = 0; j < 16; ++j)    // exact integers below 2^24: exact conversions
-                        acc[c0 + j] += (long long)__float2int_rn(__uint_as_float(p[j])) * (1LL << (24 - 8 * L));
+                        acc[a < NACC ? a : 0][c0 + j] += (long long)__float2int_rn(__uint_as_float(p[j])) * (1LL << sh);
                 }
             }
             tc_fence_before();
@@ -507,17 +556,22 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         if (!ok) atomicExch(&g_tc_status, 2);
         const int row = m0 + (warp & 3) * 32 + lane;
         if (row < M) {
-            double* crow = C + (size_t)row * ldc;
-            // 2^(e_i + f_j - 16) 2^-24; rows or columns of zeros carry a huge negative
-            // exponent (their acc is 0): clamp it so the sum cannot overflow
-            const int er = max(ea[row], -4000) - 40;
+            // 2^(e_i + f_j - 16) times the level weights; rows or columns of zeros carry a
+            // huge negative exponent (their sums are 0): clamp it so the sum cannot overflow
+            const int er = max(ea[row], -4000) - 16;
 #pragma unroll
             for (int j = 0; j < HC; ++j) {
                 const int col = n0 + cbase + j;
                 if (col < N) {
-                    double v = alpha * ldexp((double)acc[j], er + max(fb[col], -4000));
-                    if (beta != 0.0) v += beta * crow[col];
-                    crow[col] = v;
+                    const int ex = er + max(fb[col], -4000);
+                    double v = ldexp((double)acc[0][j], ex - 8 * (H - 1));
+                    if (NACC == 2) v += ldexp((double)acc[NACC - 1][j], ex - 8 * (S - 1));
+                    if (P) {
+                        P[((size_t)blockIdx.z * M + row) * N + col] = v;
+                    } else {
+                        double* dst = C + (size_t)row * ldc + col;
+                        *dst = (beta == 0.0) ? alpha * v : alpha * v + beta * (*dst);
+                    }
                 }
             }
         }
@@ -525,7 +579,21 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     tc_fence_before();
     __syncthreads();
     if (warp == OZ_PRODUCER)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(Ly::TMEM_COLS) : "memory");
+}
+
+// C = alpha sum_z P[z] + beta C (K-split partial products, summed in split order)
+__global__ void oz_reduce_kernel(const double* __restrict__ P, int splits, int M, int N, double alpha, double beta,
+                                 double* __restrict__ C, int ldc)
+{
+    const long long mn = (long long)M * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mn; e += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int z = 0; z < splits; ++z) acc += P[z * mn + e];
+        const int r = (int)(e / N), c = (int)(e % N);
+        double* dst = C + (size_t)r * ldc + c;
+        *dst = (beta == 0.0) ? alpha * acc : alpha * acc + beta * (*dst);
+    }
 }
 
 // Binary exponent of max |entry| of every row r of the logical operand X (R x K,
@@ -558,6 +626,7 @@ __global__ void oz_exponent_kernel(const double* __restrict__ X, int ld, int kco
 
 // Slices of the scaled operand: out[(q * Rp + r) * Kp + k] = a^(q)_rk (BF16 integers),
 // zero outside R x K and for rows of zeros.
+template <int S>
 __global__ void oz_slice_kernel(const double* __restrict__ X, int ld, int kcontig, int R, int K, int Rp, int Kp,
                                 const int* __restrict__ e, __nv_bfloat16* __restrict__ out)
 {
@@ -580,7 +649,7 @@ __global__ void oz_slice_kernel(const double* __restrict__ X, int ld, int kconti
         const int r = r0 + i, k = k0 + tx;
         const int er = (r < R) ? e[r] : OZ_EMPTY;
         double v = (er > OZ_EMPTY) ? ldexp(tile[i][tx], -er) : 0.0;      // |v| < 1, exact scaling
-        for (int q = 0; q < OZ_S; ++q) {
+        for (int q = 0; q < S; ++q) {
             const double t = v * 256.0;                                     // exact
             const double a = trunc(t);                                      // integer in [-255, 255]
             v = t - a;                                                      // exact remainder
@@ -589,31 +658,36 @@ __global__ void oz_slice_kernel(const double* __restrict__ X, int ld, int kconti
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-int encoder()
+// The driver's tensor-map encoder, looked up once (a function-local static is
+// initialised exactly once even when several host threads get here first).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
-    if (g_encode) return TN_OK;
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    TN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !fn) return TN_ECUDA;
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    return TN_OK;
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
 }
 
-// 2D map over a (2*rows_p) x Kp operand buffer, box = 128 bytes of K x box_rows.
-int make_map(CUtensorMap* map, int kind, void* base, int rows2, int Kp, int box_rows)
+int encoder() { return encode_fn() ? TN_OK : TN_ECUDA; }
+
+// 2D map over a rows2 x Kp operand buffer, box = row_bytes of K x box_rows, with the
+// swizzle that matches row_bytes (128 or 64 bytes).
+int make_map(CUtensorMap* map, int kind, void* base, int rows2, int Kp, int box_rows, int row_bytes = (int)ROWB)
 {
     const int esz = kind == 0 ? 4 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows2};
     cuuint64_t strides[1] = {(cuuint64_t)Kp * esz};
-    cuuint32_t box[2] = {ROWB / (cuuint32_t)esz, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(row_bytes / esz), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    CUresult r = encode_fn()(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                           base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? TN_OK : TN_ECUDA;
 }
 
@@ -631,15 +705,33 @@ int launch_tc(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int
 
 inline int round_up(int x, int q) { return (x + q - 1) / q * q; }
 
-int launch_oz(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int Mp, int Np, int nkb, int m, int n,
-              const int* ea, const int* fb, double alpha, double beta, double* C, int ldc)
+// Tile and K-split plan of a slice product.
+struct OzPlan { int Mp, Np, Kp, nkb, splits; };
+
+template <int S>
+OzPlan oz_plan(int m, int n, int k)
 {
-    static std::atomic<unsigned long long> attr{0};
-    TN_CUDA(tn_smem_optin(oz_gemm_kernel, (int)OZ_SMEM_BYTES, attr));
-    dim3 grid(Np / BN, Mp / BM);
-    oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(ma, mb, Mp, Np, nkb, m, n, ea, fb, alpha, beta, C, ldc);
-    TN_LAUNCHED();
-    return TN_OK;
+    using Cf = OzCfg<S>;
+    OzPlan p;
+    p.Mp = round_up(m, BM);
+    p.Np = round_up(n, Cf::BN);
+    p.Kp = round_up(k, Cf::KROW);
+    p.nkb = p.Kp / Cf::KROW;
+    const int tiles = (p.Mp / BM) * (p.Np / Cf::BN);
+    // products with few tiles (panels, Gram blocks) split K so that about one
+    // CTA per SM is busy; every split keeps at least two K blocks
+    p.splits = tiles >= 152 ? 1 : std::max(1, std::min(152 / tiles, p.nkb / 2));
+    return p;
+}
+
+template <int S>
+size_t oz_scratch(int m, int n, int k)
+{
+    const OzPlan p = oz_plan<S>(m, n, k);
+    size_t b = tn_align256((size_t)S * p.Mp * p.Kp * 2) + tn_align256((size_t)S * p.Np * p.Kp * 2)
+             + tn_align256((size_t)p.Mp * 4) + tn_align256((size_t)p.Np * 4);
+    if (p.splits > 1) b += tn_align256((size_t)p.splits * m * n * 8);
+    return b;
 }
 
 // Self-test of the bounded waits: one thread waits on an mbarrier that nothing
@@ -671,57 +763,71 @@ int tc_tile_n(int, int) { return BN; }
 size_t gemm_tc_scratch_bytes(int kind, int m, int n, int k)
 {
     const int bn = tc_tile_n(m, n);
-    if (kind == 2) {
-        const size_t Mp = round_up(m, BM), Np = round_up(n, bn), Kp = round_up(k, 64);
-        return tn_align256(OZ_S * Mp * Kp * 2) + tn_align256(OZ_S * Np * Kp * 2) + tn_align256(Mp * 4)
-             + tn_align256(Np * 4);
-    }
+    if (kind == 2) return oz_scratch<4>(m, n, k);
+    if (kind == 3) return oz_scratch<7>(m, n, k);
     const int kq = kind == 0 ? 32 : 64;
     const size_t esz = kind == 0 ? 4 : 2;
     const size_t Mp = round_up(m, BM), Np = round_up(n, bn), Kp = round_up(k, kq);
     return tn_align256(2 * Mp * Kp * esz) + tn_align256(2 * Np * Kp * esz);
 }
 
-// Exact-accumulation product (kind 2): exponents, slices, one tensor-core pass.
+// Exact-accumulation product (kinds 2 and 3): exponents, slices, one tensor-core
+// pass (K split over several CTAs for products with few tiles, then a sum).
+template <int S>
 static int gemm_oz(cudaStream_t st, Arena& ar, bool ta, bool tb, int m, int n, int k, double alpha,
                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc)
 {
-    const int bn = tc_tile_n(m, n);
-    const int Mp = round_up(m, BM), Np = round_up(n, bn), Kp = round_up(k, 64);
+    using Cf = OzCfg<S>;
+    using Ly = OzLayout<S>;
+    const OzPlan p = oz_plan<S>(m, n, k);
     const size_t mark = ar.mark();
-    void* As = ar.take((OZ_S * (size_t)Mp * Kp * 2 + 7) / 8);
-    void* Bs = ar.take((OZ_S * (size_t)Np * Kp * 2 + 7) / 8);
-    int* ea = reinterpret_cast<int*>(ar.take(((size_t)Mp * 4 + 7) / 8));
-    int* fb = reinterpret_cast<int*>(ar.take(((size_t)Np * 4 + 7) / 8));
-    if (!As || !Bs || !ea || !fb) { ar.release(mark); return TN_ENOMEM; }
-    // OZ_EMPTY in every byte pattern is not needed: fill with a large negative int
-    TN_CUDA(cudaMemsetAsync(ea, 0x80, (size_t)Mp * 4, st));       // 0x80808080 < OZ_EMPTY
-    TN_CUDA(cudaMemsetAsync(fb, 0x80, (size_t)Np * 4, st));
+    void* As = ar.take(((size_t)S * p.Mp * p.Kp * 2 + 7) / 8);
+    void* Bs = ar.take(((size_t)S * p.Np * p.Kp * 2 + 7) / 8);
+    int* ea = reinterpret_cast<int*>(ar.take(((size_t)p.Mp * 4 + 7) / 8));
+    int* fb = reinterpret_cast<int*>(ar.take(((size_t)p.Np * 4 + 7) / 8));
+    double* P = p.splits > 1 ? ar.take((size_t)p.splits * m * n) : nullptr;
+    if (!As || !Bs || !ea || !fb || (p.splits > 1 && !P)) { ar.release(mark); return TN_ENOMEM; }
+    TN_CUDA(cudaMemsetAsync(ea, 0x80, (size_t)p.Mp * 4, st));       // 0x80808080 < OZ_EMPTY
+    TN_CUDA(cudaMemsetAsync(fb, 0x80, (size_t)p.Np * 4, st));
     dim3 blk(32, 8);
     // A: rows m, K-contiguous unless transposed; B: rows n, K-contiguous only when transposed
-    oz_exponent_kernel<<<dim3(Kp / 32, Mp / 32), blk, 0, st>>>(A, lda, ta ? 0 : 1, m, k, ea);
+    oz_exponent_kernel<<<dim3(p.Kp / 32, p.Mp / 32), blk, 0, st>>>(A, lda, ta ? 0 : 1, m, k, ea);
     TN_LAUNCHED();
-    oz_exponent_kernel<<<dim3(Kp / 32, Np / 32), blk, 0, st>>>(B, ldb, tb ? 1 : 0, n, k, fb);
+    oz_exponent_kernel<<<dim3(p.Kp / 32, p.Np / 32), blk, 0, st>>>(B, ldb, tb ? 1 : 0, n, k, fb);
     TN_LAUNCHED();
-    oz_slice_kernel<<<dim3(Kp / 32, Mp / 32), blk, 0, st>>>(A, lda, ta ? 0 : 1, m, k, Mp, Kp, ea, (__nv_bfloat16*)As);
+    oz_slice_kernel<S><<<dim3(p.Kp / 32, p.Mp / 32), blk, 0, st>>>(A, lda, ta ? 0 : 1, m, k, p.Mp, p.Kp, ea,
+                                                                  (__nv_bfloat16*)As);
     TN_LAUNCHED();
-    oz_slice_kernel<<<dim3(Kp / 32, Np / 32), blk, 0, st>>>(B, ldb, tb ? 1 : 0, n, k, Np, Kp, fb, (__nv_bfloat16*)Bs);
+    oz_slice_kernel<S><<<dim3(p.Kp / 32, p.Np / 32), blk, 0, st>>>(B, ldb, tb ? 1 : 0, n, k, p.Np, p.Kp, fb,
+                                                                  (__nv_bfloat16*)Bs);
     TN_LAUNCHED();
     CUtensorMap ma, mb;
-    int s1 = make_map(&ma, 1, As, OZ_S * Mp, Kp, BM);
-    int s2 = make_map(&mb, 1, Bs, OZ_S * Np, Kp, bn);
+    int s1 = make_map(&ma, 1, As, S * p.Mp, p.Kp, BM, (int)Ly::ROW);
+    int s2 = make_map(&mb, 1, Bs, S * p.Np, p.Kp, Cf::BN, (int)Ly::ROW);
     if (s1 != TN_OK || s2 != TN_OK) { ar.release(mark); return TN_ECUDA; }
-    const int s = launch_oz(st, ma, mb, Mp, Np, Kp / 64, m, n, ea, fb, alpha, beta, C, ldc);
+    static std::atomic<unsigned long long> attr{0};
+    TN_CUDA(tn_smem_optin(oz_gemm_kernel<S>, (int)Ly::SMEM, attr));
+    dim3 grid(p.Np / Cf::BN, p.Mp / BM, p.splits);
+    oz_gemm_kernel<S><<<grid, OZ_THREADS, Ly::SMEM, st>>>(ma, mb, p.Mp, p.Np, p.nkb, m, n, ea, fb, alpha, beta, C,
+                                                          ldc, P);
+    TN_LAUNCHED();
+    if (P) {
+        const long long mn = (long long)m * n;
+        const int blocks = (int)std::min<long long>((mn + 255) / 256, 152 * 8);
+        oz_reduce_kernel<<<blocks, 256, 0, st>>>(P, p.splits, m, n, alpha, beta, C, ldc);
+        TN_LAUNCHED();
+    }
     ar.release(mark);       // stream-ordered: later work on this stream may reuse the buffers
-    return s;
+    return TN_OK;
 }
 
 int gemm_tc(cudaStream_t st, Arena& ar, int kind, bool ta, bool tb, int m, int n, int k, double alpha,
             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc)
 {
-    if (m < 1 || n < 1 || k < 1 || kind < 0 || kind > 2) return TN_EINVAL;
+    if (m < 1 || n < 1 || k < 1 || kind < 0 || kind > 3) return TN_EINVAL;
     TN_TRY(encoder());
-    if (kind == 2) return gemm_oz(st, ar, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (kind == 2) return gemm_oz<4>(st, ar, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (kind == 3) return gemm_oz<7>(st, ar, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     const int bn = tc_tile_n(m, n);
     const int kq = kind == 0 ? 32 : 64;
     const size_t esz = kind == 0 ? 4 : 2;

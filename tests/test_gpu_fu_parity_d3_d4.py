@@ -75,9 +75,9 @@ def oracle_case(D, chi, inst):
     return out
 
 
-def gpu_case(D, chi, inst):
+def gpu_case(D, chi, inst, precision=L.TN_F64):
     A = random_peps(2, D, instance=inst)
-    ctx = L.Context(D, chi)
+    ctx = L.Context(D, chi, precision=precision)
     ctx.tn_set_hamiltonian(1.0, H)
     ctx.tn_set_time_step(TAU)
     ctx.tn_set_state(A)
@@ -102,7 +102,7 @@ def gpu_case(D, chi, inst):
     g['ctm_k'] = ctx.tn_ctmrg(1e-12, 500)
     g['obs_k'] = ctx.tn_measure()
     ctx.close()
-    m = L.Context(D, chi)
+    m = L.Context(D, chi, precision=precision)
     m.tn_set_hamiltonian(1.0, H)
     m.tn_set_state(At)
     m.tn_build_double_layer()
@@ -211,3 +211,21 @@ def test_recycling_window(case):
     assert abs(gk['e_site'] - ok['e_site']) < E_REL * abs(ok['e_site'])
     for t in range(2):
         assert abs(abs(gk['mz'][t]) - abs(ok['mz'][t])) < 1e-9
+
+
+def test_fp64_accurate_slice_form_matches_oracle():
+    """The same step with every contraction (and the projector SVD's products) as
+    FP64-accurate 7-slice tensor-core products: the FP64 bars of the oracle parity."""
+    case = (4, 16, 12)
+    o = oracle_case(*case)
+    g = gpu_case(*case, precision=L.TN_F64S7)
+    for i, (x, y) in enumerate(SITES):
+        for c in range(4):
+            np.testing.assert_allclose(g['spectra'][i, c], o['spectra'][(x, y, 'C%d' % (c + 1))], rtol=0, atol=1e-9)
+    for e, link in enumerate(OF.link_list(CELL)):
+        assert abs(g['upd']['als_cost'][e] - o['info']['als'][link][1]) < 1e-10
+    ot, gt = o['obs_t'], g['obs_t']
+    assert abs(gt['e_site'] - ot['e_site']) < E_REL * abs(ot['e_site'])
+    ok, gk = o['obs_k'], g['obs_k']
+    assert abs(gk['e_site'] - ok['e_site']) < E_REL * abs(ok['e_site'])
+    assert abs(g['F'] - o['info']['F']) < 1e-10

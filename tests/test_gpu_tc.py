@@ -27,7 +27,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 # (relative Frobenius, elementwise vs |A||B|) per precision
-TOL = {L.TN_TF32X3: (2e-6, 2e-5), L.TN_BF16X3: (6e-5, 3e-4), L.TN_BF16S4: (1e-8, 3e-8)}
+TOL = {L.TN_TF32X3: (2e-6, 2e-5), L.TN_BF16X3: (6e-5, 3e-4), L.TN_BF16S4: (1e-8, 3e-8), L.TN_F64S7: (1e-14, 1e-14)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,7 +55,7 @@ def _run(prec, ta, tb, m, n, k, alpha=1.0, beta=0.0, inst=0):
     return dC.cpu().numpy(), ref, scale
 
 
-@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3, L.TN_BF16S4])
+@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3, L.TN_BF16S4, L.TN_F64S7])
 @pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_split_gemm_ragged(prec, ta, tb):
     """Several tiles with ragged edges in m, n and k, all transpose cases, beta != 0."""
@@ -65,7 +65,7 @@ def test_split_gemm_ragged(prec, ta, tb):
     assert np.max(np.abs(C - ref) / scale) < elem
 
 
-@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3, L.TN_BF16S4])
+@pytest.mark.parametrize("prec", [L.TN_TF32X3, L.TN_BF16X3, L.TN_BF16S4, L.TN_F64S7])
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (128, 64, 32), (1024, 1024, 1024), (1024, 80, 1024), (80, 1024, 1024)])
 def test_split_gemm_shapes(prec, m, n, k):
     """Single element, one exact tile, the enlarged-corner size N = chi D^2 = 1024 and skinny panels."""
@@ -140,3 +140,32 @@ def test_integer_slices_zero_rows_and_columns():
     np.testing.assert_array_equal(C[[0, 5, 129]], ref[[0, 5, 129]])
     np.testing.assert_array_equal(C[:, [3, 69]], ref[:, [3, 69]])
     assert np.abs(C - ref).max() < 1e-8 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m,n,k", [(1024, 112, 1024), (1024, 1024, 1024), (112, 112, 1024), (300, 70, 200)])
+def test_seven_slices_exact_on_wide_integers(m, n, k):
+    """Integers up to 2^20 need three 8-bit slices; all products and sums are exact
+    integers below 2^53, so the FP64-accurate form must reproduce them bit for bit
+    (panels and Gram blocks run with the K split and its partial sums)."""
+    rng = np.random.default_rng(m * 7 + n + k)
+    A = rng.integers(-2 ** 20, 2 ** 20 + 1, (m, k)).astype(np.float64)
+    Bm = rng.integers(-2 ** 20, 2 ** 20 + 1, (k, n)).astype(np.float64)
+    work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_F64S7, m, n, k), dtype=torch.uint8, device="cuda")
+    dC = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    L.tn_gemm_split(L.TN_F64S7, 0, 0, m, n, k, 1.0, _dev(A), k, _dev(Bm), n, 0.0, dC, n, work)
+    assert np.array_equal(dC.cpu().numpy(), A @ Bm)
+
+
+def test_seven_slices_match_fp64_on_graded_rows():
+    """Rows and columns spanning 12 orders of magnitude: relative to each entry's own
+    scale (|A||B|) the error stays at the FP64 level."""
+    m, n, k = 256, 192, 512
+    rng = np.random.default_rng(5)
+    A = random_matrix((m, k), instance=44) * 10.0 ** rng.uniform(-6, 6, (m, 1))
+    Bm = random_matrix((k, n), instance=45) * 10.0 ** rng.uniform(-6, 6, (1, n))
+    work = torch.empty(L.tn_gemm_split_workspace_bytes(L.TN_F64S7, m, n, k), dtype=torch.uint8, device="cuda")
+    dC = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    L.tn_gemm_split(L.TN_F64S7, 0, 0, m, n, k, 1.0, _dev(A), k, _dev(Bm), n, 0.0, dC, n, work)
+    err = np.abs(dC.cpu().numpy() - A @ Bm)
+    assert np.all(err <= 2.0 ** -50 * k * np.outer(np.abs(A).max(axis=1), np.abs(Bm).max(axis=0))
+                  + 1e-15 * np.abs(A) @ np.abs(Bm))
