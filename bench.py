@@ -8,9 +8,10 @@ checkerboard iPEPS, D = 4, chi = 64:
   a warm-started CTMRG run to convergence (corner spectra change < CTM_TOL,
   at most CTM_MAX iterations of 4 directional moves),
   bond environments + ALS + assembly of every link type.
-The headline is the precision form HEADLINE (the CTMRG contractions on the
-tensor cores; projector SVD, bond environment, ALS, gauge fixing in FP64);
-the plain FP64 form and the other split forms are timed on the same steps
+The headline is the precision form HEADLINE: the CTMRG contractions as
+exact-accumulation BF16 slice products on the tensor cores with 7 slices,
+accurate to FP64 (projector SVD, bond environment, ALS, gauge fixing in
+FP64); the plain FP64 form and the other forms are timed on the same steps
 from the same state and reported beside it.  The measured CTMRG iterations
 per step (k_ctm) are part of the line; the fixed-budget step of earlier
 measurements (FIXED_CTM_ITERS iterations, no convergence test) is a
@@ -43,13 +44,14 @@ CTM_MAX = 40                        # iteration cap of the convergence-driven CT
 CTM_TOL = {"f64": 1e-8, "f64s7": 1e-8, "bf16s4": 1e-7, "tf32x3": 1e-6, "bf16x3": 1e-5}
 FIXED_CTM_ITERS = 4                 # the secondary fixed-budget step
 N_RE = 5                            # recycled steps per environment computation (Sec. VI.C)
-HEADLINE = "bf16s4"
+HEADLINE = "f64s7"
 PRECISIONS = {"f64": 0, "tf32x3": 1, "bf16x3": 2, "bf16s4": 3, "f64s7": 4}
-FORMS = ("bf16s4", "f64", "f64s7", "tf32x3", "bf16x3")
-MAIN_FORMS = ("bf16s4", "f64", "f64s7")      # timed with the full schedule; the others on fewer steps
+FORMS = ("f64s7", "f64", "bf16s4", "tf32x3", "bf16x3")
+MAIN_FORMS = ("f64s7", "f64", "bf16s4")      # timed with the full schedule; the others on fewer steps
 # moves per converged step, for the reference arm's extrapolation: 4 x the warm-started
-# k_ctm the GPU arm measures on this workload (3.0 on GB300, see the bench line's "k_ctm")
-REF_MOVES_PER_STEP = 12
+# k_ctm the GPU arm measures on this workload at tol 1e-8 (17.3 and 17.7 iterations per
+# step in the FP64-accurate forms on GB300, see the bench line's "k_ctm")
+REF_MOVES_PER_STEP = 70
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor rate
 FP64_PROBE_ITERS = 4096
 
@@ -221,21 +223,21 @@ def energy_error_small(L, precision):
     ctx.tn_set_time_step(tau)
     ctx.tn_set_state(A)
     cfg = OR.Config(h=h, tau=tau, D=D, chi=chi, ctm_tol=1e-10, ctm_max=500)
-    ctm_tol = 1e-10 if precision in (L.TN_F64, L.TN_BF16S4) else 1e-8
+    ctm_tol = 1e-10 if precision in (L.TN_F64, L.TN_BF16S4, L.TN_F64S7) else 1e-8
     env, Ao = None, A
     for _ in range(3):
         ctx.tn_fu_step(ctm_tol, 500)
         Ao, env, _ = OR.fu_step(Ao, OC.checkerboard(), cfg, env)
     ctx.tn_build_double_layer()
     ctx.tn_reset_env()
-    ctx.tn_ctmrg(1e-12 if precision in (L.TN_F64, L.TN_BF16S4) else 1e-8, 500)
+    ctx.tn_ctmrg(1e-12 if precision in (L.TN_F64, L.TN_BF16S4, L.TN_F64S7) else 1e-8, 500)
     g = ctx.tn_measure()
     o = OR.energy(Ao, OC.checkerboard(), cfg, tol=1e-12)
     ctx.close()
     return abs(g["e_site"] - o["e_site"]) / abs(o["e_site"]), g["e_site"], o["e_site"]
 
 
-def time_form(L, torch, dev, stream, name, state, args, flush, steps, recycled=True, fixed=True):
+def time_form(L, torch, dev, stream, name, state, warmup, flush, steps, recycled=True, fixed=True):
     """Warm-up, then `steps` timed converged steps (and optionally `steps` recycled windows
     and `steps` fixed-budget steps) of one precision form."""
     D, chi = WL["D"], WL["chi"]
@@ -244,7 +246,7 @@ def time_form(L, torch, dev, stream, name, state, args, flush, steps, recycled=T
     ctx.tn_set_hamiltonian(1.0, WL["h"])
     ctx.tn_set_time_step(WL["tau"])
     ctx.tn_set_state(state)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.tn_fu_step(tol, CTM_MAX)
     t_prep = t_ctm = t_upd = 0.0
     launches = svd_calls = svd_iters = ctm_iters = nonconv = 0
@@ -272,7 +274,7 @@ def time_form(L, torch, dev, stream, name, state, args, flush, steps, recycled=T
         t_upd += ev[2].elapsed_time(ev[3]) / 1e3
     out = dict(total=t_prep + t_ctm + t_upd, t_prep=t_prep, t_ctm=t_ctm, t_upd=t_upd, launches=launches,
                svd_calls=svd_calls, svd_iters=svd_iters, ctm_iters=ctm_iters, nonconverged=nonconv, steps=steps,
-               ctm_tol=tol)
+               ctm_tol=tol, steps_total=warmup + steps)
     import numpy as np
     out["state"] = [np.ascontiguousarray(a) for a in ctx.tn_get_state()]    # after the converged steps
     if fixed:
@@ -393,7 +395,7 @@ def run_gpu(args):
         A = torch.randn(N, N, dtype=torch.float64, device=dev)
         B = torch.randn(N, N, dtype=torch.float64, device=dev)
         C = torch.empty(N, N, dtype=torch.float64, device=dev)
-        for prec in (L.TN_TF32X3, L.TN_BF16S4):
+        for prec in (L.TN_TF32X3, L.TN_BF16S4, L.TN_F64S7):
             work = torch.empty(L.tn_gemm_split_workspace_bytes(prec, N, N, N), dtype=torch.uint8, device=dev)
             for _ in range(3):
                 L.tn_gemm_split(prec, 0, 0, N, N, N, 1.0, A, N, B, N, 0.0, C, N, work, stream)
@@ -454,7 +456,8 @@ def run_gpu(args):
         for name in FORMS:
             main = name in MAIN_FORMS
             steps = args.steps if main else max(1, min(args.steps, 3))
-            ctxs[name], results[name] = time_form(L, torch, dev, stream, name, state, args, flush, steps,
+            warm = args.warmup if main else min(args.warmup, 1)
+            ctxs[name], results[name] = time_form(L, torch, dev, stream, name, state, warm, flush, steps,
                                                   recycled=name in (HEADLINE, "f64"), fixed=name == HEADLINE)
     head = results[HEADLINE]
     total, t_ctm = max_over_ranks([head["total"], head["t_ctm"]], dist, dev)
@@ -490,7 +493,7 @@ def run_gpu(args):
         m, _ = converged_energy(L, dev, PRECISIONS[name], results["f64"]["state"], tol=max(1e-9, CTM_TOL[name]))
         env_e[name] = m["e_site"]
         env_err[name] = abs(m["e_site"] - e_ref["e_site"]) / abs(e_ref["e_site"])
-        if results[name]["steps"] == results["f64"]["steps"]:
+        if results[name]["steps_total"] == results["f64"]["steps_total"]:     # the same evolution
             t, _ = converged_energy(L, dev, L.TN_F64, results[name]["state"])
             traj_err[name] = {"e_site": abs(t["e_site"] - e_ref["e_site"]) / abs(e_ref["e_site"]),
                               "mx": max(abs(a - b) for a, b in zip(t["mx"], e_ref["mx"])),
@@ -505,7 +508,7 @@ def run_gpu(args):
     t_dgemm = kernel_time(torch, stream, lambda: L.tn_gemm_f64(0, 0, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, 0, 1,
                                                               stream))
     t_tc = {}
-    for name in ("tf32x3", "bf16x3", "bf16s4"):
+    for name in ("tf32x3", "bf16x3", "bf16s4", "f64s7"):
         prec = PRECISIONS[name]
         work = torch.empty(L.tn_gemm_split_workspace_bytes(prec, N, N, N), dtype=torch.uint8, device=dev)
         t_tc[name] = kernel_time(torch, stream, lambda: L.tn_gemm_split(prec, 0, 0, N, N, N, 1.0, A, N, B, N, 0.0,
@@ -524,7 +527,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16-slices+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x7-slices(int64 acc)+f64", "data": "synthetic",
         "moves_per_s": world * 4 * head["ctm_iters"] / t_ctm,
         "k_ctm": hs["k_ctm"], "ctm_tol": CTM_TOL[HEADLINE], "ctm_max": CTM_MAX,
         "nonconverged_steps": hs["nonconverged_steps"],
@@ -541,13 +544,16 @@ def run_gpu(args):
                 "d2h_bytes_per_step": state_bytes},
         "gpu_launches": int(head["launches"]),
         "clocks": csum,
-        "roofline": {"bound": "tensor", "kernel": "oz_gemm_kernel (BF16 integer slices) %dx%dx%d incl. exponent "
-                                                  "and slice passes, launched alone at the step's shape" % (N, N, N),
-                     "achieved": method_flop / t_tc["bf16s4"] / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
-                     "frac": method_flop / t_tc["bf16s4"] / 1e12 / bf16_peak, "traffic": None,
+        "roofline": {"bound": "tensor", "kernel": "oz_gemm_kernel<7> (7 BF16 integer slices, FP64-accurate) "
+                                                  "%dx%dx%d incl. exponent and slice passes, launched alone at the "
+                                                  "step's N^3 shape" % (N, N, N),
+                     "achieved": method_flop / t_tc["f64s7"] / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": method_flop / t_tc["f64s7"] / 1e12 / bf16_peak, "traffic": None,
                      "flop_basis": "method FLOPs 2N^3 of the FP64 product it delivers; the tensor pipe executes "
-                                   "10 slice products (20 N^3)",
-                     "peak_source": "bf16_tflops burst, " + peak_src, "ms": t_tc["bf16s4"] * 1e3},
+                                   "28 slice products (56 N^3)",
+                     "pipe_frac": 28 * method_flop / t_tc["f64s7"] / 1e12 / bf16_peak,
+                     "vs_fp64_peak": method_flop / t_tc["f64s7"] / 1e12 / fp64_tflops,
+                     "peak_source": "bf16_tflops burst, " + peak_src, "ms": t_tc["f64s7"] * 1e3},
         "roofline_fp64": {"bound": "alu", "kernel": "dgemm_kernel %dx%dx%d (FP64 SIMT; GB300 has no FP64 tensor "
                                                     "path)" % (N, N, N),
                           "achieved": method_flop / t_dgemm / 1e12, "peak": fp64_tflops, "unit": "TFLOP/s",
@@ -564,7 +570,7 @@ def run_gpu(args):
                        "trajectory_workload": "each form's own state after the same converged steps from the same "
                                               "seeded start, CTMRG and observables in FP64"},
     }
-    for name in ("f64", HEADLINE, "tf32x3"):
+    for name in ("f64", HEADLINE, "bf16s4", "tf32x3"):
         try:
             err, eg, eo = energy_error_small(L, PRECISIONS[name])
             line["energy_err"]["vs_oracle_" + name] = {"rel": err, "e_gpu": eg, "e_oracle": eo,
@@ -582,8 +588,8 @@ def workload_config(world):
     return dict(workload="ITE full-update step, 2D TFIM h=3.04 tau=0.005, checkerboard iPEPS D=4 chi=64, "
                          "from the seeded Gaussian tensors; warm CTMRG converged per step (corner-spectrum change "
                          "< %g, cap %d iterations); precision form: CTMRG contractions as exact-accumulation BF16 "
-                         "slice products on the tensor cores, projector SVD / bond environment / ALS / gauge fix "
-                         "FP64" % (CTM_TOL[HEADLINE], CTM_MAX),
+                         "slice products on the tensor cores (7 slices, FP64-accurate), projector SVD / bond "
+                         "environment / ALS / gauge fix FP64" % (CTM_TOL[HEADLINE], CTM_MAX),
                 **WL, ctm_tol=CTM_TOL[HEADLINE], ctm_max=CTM_MAX, start="seeded Gaussian tensors",
                 parallelism="replicas" if world > 1 else "single", l2="flushed between timed steps (256 MB write)")
 

@@ -239,6 +239,26 @@ typedef struct tn_evolve_report {
  * error; TN_ENUMERIC when a plain step produces a NaN/Inf. */
 int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* opts, tn_evolve_report* rep);
 
+/* Batched form (no counterpart in the paper: many independent instances, e.g.
+ * several fields h, bond dimensions D and chi, at once).  ctxs: n_ctx contexts
+ * created by the caller, each with its own CUDA stream (TN_EINVAL if two share
+ * a context or a stream); every one is evolved n_steps with the same options
+ * by a pool of min(n_threads, n_ctx) host threads (n_threads <= 0: one per
+ * context), so the kernels of different instances run concurrently on the
+ * GPU.  statuses[i], reps[i] (optional, n_ctx entries) receive each tn_evolve
+ * result.  Returns TN_OK when every instance returned TN_OK or TN_EUNSTABLE,
+ * else the first other status.  No other thread may use the contexts while
+ * the call runs. */
+int tn_evolve_batch(void** ctxs, int n_ctx, int n_steps, const tn_evolve_opts* opts, int n_threads,
+                    int* statuses, tn_evolve_report* reps);
+
+/* Tile autotuner of the FP64 SIMT products (process-wide; off by default).
+ * With it on, the first product of each shape with beta = 0 times the tile
+ * edges 16, 32 and 64 and keeps the fastest for that shape (the shapes follow
+ * D and chi); every tile sums in the same order, so results do not change.
+ * Returns the number of shapes tuned so far. */
+int tn_set_autotune(int enable);
+
 /* ---- observables (Sec. VI.D; row a14) ----------------------------------- */
 typedef struct tn_observables {
     double e_site;    /* -(1/n) sum_links <ZZ> J - h (1/n) sum_t <X>_t */
@@ -252,6 +272,28 @@ typedef struct tn_observables {
  * be the environment of the state's own double layers: call
  * tn_build_double_layer + tn_ctmrg first). */
 int tn_measure(void* ctx, tn_observables* obs);
+
+/* ---- 1D iMPS (Sec. III and V: the chain, where the method has an exact answer) ----
+ * One-site iMPS A[s][l][r] (d = 2, bond chi, 1 <= chi <= 16) in device memory,
+ * transverse-field Ising chain H = -sum Z Z - h sum X.  work: device scratch
+ * of at least tn_imps_workspace_bytes(chi) bytes (caller owned, any alignment;
+ * the library aligns inside it); stream: cudaStream_t (NULL = legacy default);
+ * each call synchronises it.  TN_EINVAL for chi outside 1..16, tau <= 0 or a
+ * non-finite h; TN_ENOMEM for a short workspace. */
+size_t tn_imps_workspace_bytes(int chi);
+/* n_steps plain iTEBD steps with the iMPO (Sec. V.A): A <- Q (g A) P, the
+ * optimal truncation through the canonical form of g A (Sec. III), unit norm. */
+int tn_imps_itebd(double* dA, int chi, double h, double tau, int n_steps, void* work, size_t bytes, void* stream);
+/* One recycling window (Sec. V.B): A_0 = weighted canonical form of A; one
+ * plain step gives A~ = Q (g A_0) P; the canonical form of A~ gives its maps;
+ * gauge fixing finds U with A~_1 ~ U A_0 U^T (fidelity F, optional out); the
+ * renormalised gate G = U^T Q_c Q g P P_c U is applied n_re times to A_0.
+ * A is replaced by A_{n_re}. */
+int tn_imps_recycle(double* dA, int chi, double h, double tau, int n_re, double* fidelity, void* work,
+                    size_t bytes, void* stream);
+/* <ZZ>, <X> and the energy per site e = -<ZZ> - h <X> of A (out[0..2], host),
+ * from its canonical form. */
+int tn_imps_observables(const double* dA, int chi, double h, double* out, void* work, size_t bytes, void* stream);
 
 /* ---- intermediate tensors (for checkpoints and parity checks) ----------- */
 #define TN_T_STATE      0   /* A per tensor id: d*D^4 */

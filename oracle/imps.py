@@ -89,14 +89,18 @@ def truncate(Theta, chi):
     return At / np.linalg.norm(At), P, Q
 
 
-def gauge_fix(A, B, tol=1e-12, max_iter=2000):
+def gauge_fix(A, B, tol=1e-12, max_iter=2000, U0=None):
     """U (orthogonal) maximising F = sum_s Tr(U A^s U^T B^{sT}); returns U, F.
 
     Reading of the stopping rule: F is quadratic in the error of U near its
     maximum, so the iteration stops when U itself changes by less than tol.
+    Start: U0 (default the identity).  The iteration U <- polar(M)^T only
+    climbs to the nearest local maximum; which one depends on the sign and
+    basis conventions of the two canonical forms, so a start that does not
+    depend on them matters (see recycle_window).
     """
     chi = A.shape[1]
-    U = np.eye(chi)
+    U = np.eye(chi) if U0 is None else np.array(U0, dtype=float)
     for _ in range(max_iter):
         M = np.einsum('sab,cb,sdc->ad', A, U, B)     # M = sum_s A^s U^T B^{sT}
         W, S, Vt = np.linalg.svd(M)
@@ -140,8 +144,14 @@ def recycle_window(A, h, delta, chi, n_re):
     Theta = apply_mpo(g, A0)
     At, P, Q = truncate(Theta, chi)
     _, lam1, MLc, MRc, A1 = canonicalize(At)
-    U, F = gauge_fix(A0, A1)
     s1 = np.sqrt(lam1)
+    # start of the gauge fix (the paper does not give one): for small delta the kappa = 0
+    # block of Theta = g A_0 is A_0 up to a factor, so A_1 = Q_c A~ P_c ~ L0 A_0 (...) with
+    # the leg map L0 = Q_c Q[:, kappa = 0]; its polar factor is the gauge up to the
+    # truncation.  From the identity the iteration can stop in a local maximum
+    # (F = 0.44 against 0.989 at h = 2, chi = 6).
+    W0, _, V0t = np.linalg.svd((s1[:, None] * MLc) @ Q[:, :chi])
+    U, F = gauge_fix(A0, A1, U0=W0 @ V0t)
     KL = U.T @ (s1[:, None] * MLc) @ Q      # chi x kappa*chi: U^T Q_c Q
     KR = P @ (MRc * s1[None, :]) @ U        # kappa*chi x chi: P P_c U
     Ak = A0

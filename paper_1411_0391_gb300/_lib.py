@@ -85,6 +85,14 @@ _SIGS = {
     "tn_recycle": (c_int, [c_void_p, c_int, _DP]),
     "tn_evolve": (c_int, [c_void_p, c_int, POINTER(tn_evolve_opts), POINTER(tn_evolve_report)]),
     "tn_measure": (c_int, [c_void_p, POINTER(tn_observables)]),
+    "tn_evolve_batch": (c_int, [POINTER(c_void_p), c_int, c_int, POINTER(tn_evolve_opts), c_int, POINTER(c_int),
+                                POINTER(tn_evolve_report)]),
+    "tn_set_autotune": (c_int, [c_int]),
+    "tn_imps_workspace_bytes": (c_size_t, [c_int]),
+    "tn_imps_itebd": (c_int, [c_void_p, c_int, c_double, c_double, c_int, c_void_p, c_size_t, c_void_p]),
+    "tn_imps_recycle": (c_int, [c_void_p, c_int, c_double, c_double, c_int, POINTER(c_double), c_void_p, c_size_t,
+                                c_void_p]),
+    "tn_imps_observables": (c_int, [c_void_p, c_int, c_double, POINTER(c_double), c_void_p, c_size_t, c_void_p]),
     "tn_get_tensor": (c_int, [c_void_p, c_int, c_int, _DP, c_size_t]),
     "tn_gemm_f64": (c_int, [c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_longlong,
                             c_void_p, c_int, c_longlong, c_double, c_void_p, c_int, c_longlong, c_int, c_void_p]),
@@ -211,6 +219,79 @@ def tn_truncated_svd_noalloc(M, m, k, U, S, V, warm=None, stream=None):
                                                  c_void_p(0 if warm is None else warm.data_ptr()),
                                                  _stream_ptr(stream)),
                   "tn_truncated_svd_noalloc", allow_noconv=True)
+
+
+def tn_set_autotune(enable):
+    """Turn the FP64 product tile autotuner on or off; returns the shapes tuned so far."""
+    return int(lib().tn_set_autotune(1 if enable else 0))
+
+
+def _evolve_opts(n_re, recycle, ctm_tol, ctm_max, recycle_eps, check_every, warmup_plain, als_tol, als_max,
+                 min_fidelity):
+    mode = TN_RECYCLE_THRESHOLD if recycle == "threshold" else (TN_RECYCLE_FIXED if recycle else TN_RECYCLE_OFF)
+    eps = float("inf") if recycle_eps is None else recycle_eps
+    return tn_evolve_opts(mode, n_re, ctm_tol, ctm_max, eps, check_every, warmup_plain, als_tol, als_max,
+                          min_fidelity)
+
+
+def _report(rep, s):
+    return dict(steps=rep.steps, env_computations=rep.env_computations, ctm_iterations=rep.ctm_iterations,
+                ctm_moves=rep.ctm_moves, nonconverged=rep.nonconverged, last_fidelity=rep.last_fidelity,
+                checks=rep.checks, last_change=rep.last_change, fallbacks=rep.fallbacks,
+                final_n_re=rep.final_n_re, status=s)
+
+
+def tn_evolve_batch(contexts, n_steps, recycle=False, n_re=1, ctm_tol=1e-10, ctm_max=500, recycle_eps=None,
+                    check_every=1, warmup_plain=0, als_tol=1e-12, als_max=50, min_fidelity=0.0, n_threads=0):
+    """Evolve independent contexts (each on its own stream) concurrently; one report per context."""
+    n = len(contexts)
+    arr = (c_void_p * n)(*[c.handle for c in contexts])
+    o = _evolve_opts(n_re, recycle, ctm_tol, ctm_max, recycle_eps, check_every, warmup_plain, als_tol, als_max,
+                     min_fidelity)
+    st = (c_int * n)()
+    reps = (tn_evolve_report * n)()
+    _check(lib().tn_evolve_batch(arr, n, n_steps, byref(o), n_threads, st, reps), "tn_evolve_batch")
+    return [_report(reps[i], st[i]) for i in range(n)]
+
+
+class IMPS:
+    """A one-site iMPS on the GPU (1D chain, Sec. III and V): device tensor + workspace (torch)."""
+
+    def __init__(self, A, device="cuda:0", stream=None):
+        import torch
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        self.chi = int(A.shape[1])
+        nbytes = int(lib().tn_imps_workspace_bytes(self.chi))
+        if nbytes == 0:
+            raise TnError(TN_EINVAL, "tn_imps_workspace_bytes")
+        self.A = torch.from_numpy(A).to(device)
+        self.work = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream
+
+    def _w(self):
+        return c_void_p(self.work.data_ptr()), self.work.numel()
+
+    def tn_imps_itebd(self, h, tau, n_steps):
+        w, nb = self._w()
+        _check(lib().tn_imps_itebd(c_void_p(self.A.data_ptr()), self.chi, h, tau, n_steps, w, nb,
+                                   _stream_ptr(self.stream)), "tn_imps_itebd")
+
+    def tn_imps_recycle(self, h, tau, n_re):
+        F = c_double(0.0)
+        w, nb = self._w()
+        _check(lib().tn_imps_recycle(c_void_p(self.A.data_ptr()), self.chi, h, tau, n_re, byref(F), w, nb,
+                                     _stream_ptr(self.stream)), "tn_imps_recycle")
+        return F.value
+
+    def tn_imps_observables(self, h):
+        out = (c_double * 3)()
+        w, nb = self._w()
+        _check(lib().tn_imps_observables(c_void_p(self.A.data_ptr()), self.chi, h, out, w, nb,
+                                         _stream_ptr(self.stream)), "tn_imps_observables")
+        return dict(zz=out[0], x=out[1], e=out[2])
+
+    def state(self):
+        return self.A.cpu().numpy()
 
 
 # ---- context -----------------------------------------------------------------
@@ -344,18 +425,13 @@ class Context:
         """recycle: False/True (fixed windows of n_re) or "threshold" (windows of at most n_re,
         ended when the bond environment drifts by more than recycle_eps).  The returned
         "status" is TN_OK or TN_EUNSTABLE (windows redone without recycling: "fallbacks")."""
-        mode = TN_RECYCLE_THRESHOLD if recycle == "threshold" else (TN_RECYCLE_FIXED if recycle else TN_RECYCLE_OFF)
-        eps = float("inf") if recycle_eps is None else recycle_eps
-        o = tn_evolve_opts(mode, n_re, ctm_tol, ctm_max, eps, check_every, warmup_plain, als_tol, als_max,
-                           min_fidelity)
+        o = _evolve_opts(n_re, recycle, ctm_tol, ctm_max, recycle_eps, check_every, warmup_plain, als_tol, als_max,
+                         min_fidelity)
         rep = tn_evolve_report()
         s = lib().tn_evolve(self.handle, n_steps, byref(o), byref(rep))
         if s != TN_EUNSTABLE:
             _check(s, "tn_evolve")
-        return dict(steps=rep.steps, env_computations=rep.env_computations, ctm_iterations=rep.ctm_iterations,
-                    ctm_moves=rep.ctm_moves, nonconverged=rep.nonconverged, last_fidelity=rep.last_fidelity,
-                    checks=rep.checks, last_change=rep.last_change, fallbacks=rep.fallbacks,
-                    final_n_re=rep.final_n_re, status=s)
+        return _report(rep, s)
 
     def tn_set_projector_cutoff(self, cut):
         _check(lib().tn_set_projector_cutoff(self.handle, cut), "tn_set_projector_cutoff")

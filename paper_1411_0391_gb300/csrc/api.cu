@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <new>
 #include <atomic>
+#include <thread>
 #include "ctx.cuh"
 
 namespace tn {
@@ -66,7 +67,10 @@ static bool plan(Ctx& c)
     c.envbuf = take(c.env_size());
     for (int r = 0; r < 4; ++r)
         for (int x = 0; x < 2; ++x)
-            for (int y = 0; y < 2; ++y) c.warmV[r][x][y] = take(N * chi);
+            for (int y = 0; y < 2; ++y) {
+                c.warmV[r][x][y] = take(N * chi);
+                c.warmB[r][x][y] = take(N * (size_t)tsvd_columns((int)N, chi));
+            }
     for (int y = 0; y < 4; ++y) { c.Pup[y] = take(N * chi); c.Plo[y] = take(N * chi); }
     c.dscratch = take(64);
     c.scratch_base = ar.mark();
@@ -541,6 +545,47 @@ int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* o, tn_evolve_report*
     TN_CUDA(cudaStreamSynchronize(c.st));
     if (rep) *rep = r;
     return r.fallbacks ? TN_EUNSTABLE : TN_OK;
+}
+
+// Batched form: independent contexts evolved concurrently, one host thread per
+// context at a time, each context on its own stream (so their kernels overlap).
+int tn_evolve_batch(void** ctxs, int n_ctx, int n_steps, const tn_evolve_opts* opts, int n_threads, int* statuses,
+                    tn_evolve_report* reps)
+{
+    if (!ctxs || n_ctx < 1 || !opts || n_steps < 0) return TN_EINVAL;
+    for (int i = 0; i < n_ctx; ++i) {
+        if (!ctxs[i]) return TN_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i] || (C(ctxs[j])->st == C(ctxs[i])->st)) return TN_EINVAL;   // shared stream
+    }
+    int dev = 0;
+    TN_CUDA(cudaGetDevice(&dev));
+    const int nt = std::max(1, std::min(n_threads > 0 ? n_threads : n_ctx, n_ctx));
+    std::atomic<int> next{0};
+    std::vector<int> st(n_ctx, TN_OK);
+    std::vector<tn_evolve_report> rp(n_ctx);
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        for (int i = next.fetch_add(1); i < n_ctx; i = next.fetch_add(1))
+            st[i] = tn_evolve(ctxs[i], n_steps, opts, &rp[i]);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+    int first = TN_OK;
+    for (int i = 0; i < n_ctx; ++i) {
+        if (statuses) statuses[i] = st[i];
+        if (reps) reps[i] = rp[i];
+        if (first == TN_OK && st[i] != TN_OK && st[i] != TN_EUNSTABLE) first = st[i];
+    }
+    return first;
+}
+
+int tn_set_autotune(int enable)
+{
+    set_autotune(enable);
+    return autotune_entries();
 }
 
 int tn_measure(void* ctx, tn_observables* obs)

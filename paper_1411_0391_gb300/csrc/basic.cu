@@ -6,6 +6,9 @@
 // kernel whose only job is to keep the FP64 units busy: 64x64 output tiles
 // (32x32 or 16x16 when the product has few tiles), 16-deep k slices staged in
 // shared memory, 4x4 (2x2, 1x1) outputs per thread.
+#include <array>
+#include <map>
+#include <mutex>
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -102,6 +105,71 @@ static int gemm_tile(int m, int n, int batch)
     return 16;
 }
 
+// ---------------------------------------------------------------------------
+// Tile autotuner: with tuning on, the first product of each shape (m, n, k,
+// transposes, batch) with beta = 0 times the three tile edges on its own
+// stream (each candidate overwrites C with the same values: every tile sums
+// k in the same order, so the results are bitwise identical) and keeps the
+// fastest for that shape; later products of the shape use it.  Shapes follow
+// (D, chi), so this picks tiles per (D, chi).  Off by default.
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_autotune{0};
+static std::mutex g_tune_mu;
+static std::map<std::array<long long, 6>, int> g_tune;
+
+void set_autotune(int on) { g_autotune.store(on ? 1 : 0); }
+int autotune_entries()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (int)g_tune.size();
+}
+
+static void launch_tile(int t, cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
+                        const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
+                        double beta, double* C, int ldc, long long sC, int batch)
+{
+    if (t == 64) launch_dgemm<64>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+    else if (t == 32) launch_dgemm<32>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+    else launch_dgemm<16>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+}
+
+static int tuned_tile(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
+                      const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
+                      double* C, int ldc, long long sC, int batch, int* tile)
+{
+    const std::array<long long, 6> key = {m, n, k, (ta ? 1 : 0) + (tb ? 2 : 0), batch, 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) { *tile = it->second; return TN_OK; }
+    }
+    const int cand[3] = {16, 32, 64};
+    float best = 1e30f;
+    int pick = gemm_tile(m, n, batch);
+    cudaEvent_t e0, e1;
+    TN_CUDA(cudaEventCreate(&e0));
+    TN_CUDA(cudaEventCreate(&e1));
+    for (int c = 0; c < 3; ++c) {
+        if ((m + cand[c] - 1) / cand[c] > 65535) continue;
+        TN_CUDA(cudaEventRecord(e0, st));
+        launch_tile(cand[c], st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, 0.0, C, ldc, sC, batch);
+        TN_LAUNCHED();
+        TN_CUDA(cudaEventRecord(e1, st));
+        TN_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        TN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; pick = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = pick;
+    }
+    *tile = pick;
+    return TN_OK;
+}
+
 int gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
          const double* A, int lda, long long sA, const double* B, int ldb, long long sB,
          double beta, double* C, int ldc, long long sC, int batch)
@@ -114,11 +182,11 @@ int gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, double alpha,
         return TN_OK;
     }
     if (batch > 65535) return TN_EINVAL;
-    const int t = gemm_tile(m, n, batch);
+    int t = gemm_tile(m, n, batch);
+    if (beta == 0.0 && g_autotune.load(std::memory_order_relaxed))
+        TN_TRY(tuned_tile(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, &t));
     if ((m + t - 1) / t > 65535) return TN_EINVAL;
-    if (t == 64) launch_dgemm<64>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
-    else if (t == 32) launch_dgemm<32>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
-    else launch_dgemm<16>(st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+    launch_tile(t, st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
     TN_LAUNCHED();
     return TN_OK;
 }

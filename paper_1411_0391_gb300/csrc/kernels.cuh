@@ -22,6 +22,8 @@ int fill(cudaStream_t st, double* x, long long n, double v);
 int hash_fill(cudaStream_t st, double* x, long long n, unsigned long long seed);
 int axpby(cudaStream_t st, double* y, const double* x, long long n, double a, double b);
 int dfma_probe(cudaStream_t st, int iters, double* flops);   // FP64 FMA rate probe (no sync)
+void set_autotune(int on);                                   // DGEMM tile autotuner on/off
+int autotune_entries();                                      // shapes tuned so far
 
 // linalg.cu
 int svd_small(cudaStream_t st, const double* A, int m, int n, int batch, double* U, double* S, double* V);
@@ -40,7 +42,7 @@ int svd_mixed(cudaStream_t st, Arena& ar, const double* B, int n, double* U, dou
 // stopping threshold relative to the largest singular value.
 int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
                   double* U, double* S, double* V, const double* warm, TsvdStats* stats,
-                  int kind = -1, double tol = 1e-13);
+                  int kind = -1, double tol = 1e-13, double* basis = nullptr, bool basis_valid = false);
 
 // tc_gemm.cu: split-precision products on the tensor cores (kind 0 = TF32 x3,
 // 1 = BF16 x3); tc_status reads and clears the device-side wait flag.

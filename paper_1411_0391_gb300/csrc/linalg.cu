@@ -89,19 +89,21 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(const double* __restrict_
         double c_shift, double* __restrict__ Xout)
 {
     extern __shared__ double sm[];
-    double* G = sm;              // n*n
-    double* X = G + n * n;       // n*n
-    int* dead = (int*)(X + n * n);
+    const int ld = n | 1;        // odd row stride (see blk_chol_inv)
+    double* G = sm;              // n*ld
+    double* X = G + n * ld;      // n*ld scratch
+    int* dead = (int*)(X + n * ld);
     __shared__ double red[32];
     double tr = 0.0;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        G[e] = Gin[e];
-        if (e % n == e / n) tr += Gin[e];
+        const int i = e / n, j = e % n;
+        G[i * ld + j] = Gin[e];
+        if (i == j) tr += Gin[e];
     }
     tr = block_sum(tr, red);
     const double shift = c_shift * 1.1102230246251565e-16 * tr;
     double dmax = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) { G[i * n + i] += shift; dmax = fmax(dmax, G[i * n + i]); }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { G[i * ld + i] += shift; dmax = fmax(dmax, G[i * ld + i]); }
     __syncthreads();
     dmax = warp_max(dmax);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
@@ -112,11 +114,11 @@ __global__ void __launch_bounds__(512) chol_inv_kernel(const double* __restrict_
         red[0] = m;
     }
     __syncthreads();
-    blk_chol_inv<double>(G, n, 1e-26 * red[0], X, dead);     // X: scratch; the inverse lands in G
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xout[e] = G[e];
+    blk_chol_inv<double>(G, n, ld, 1e-26 * red[0], X, dead);     // X: scratch; the inverse lands in G
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xout[e] = G[(e / n) * ld + e % n];
 }
 
-static size_t chol_smem(int n) { return sizeof(double) * 2 * (size_t)n * n + sizeof(int) * n + 64; }
+static size_t chol_smem(int n) { return sizeof(double) * 2 * (size_t)n * (n | 1) + sizeof(int) * n + 64; }
 
 int chol_inv(cudaStream_t st, const double* G, int n, double c_shift, double* X)
 {
@@ -228,13 +230,17 @@ int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols
 //   pair has || M v_i - s_i u_i || = || T vb_i - s_i u_i || <= tol s_1 (an
 //   absolute test: directions at the noise floor pass it too; tol = 1e-13 in
 //   FP64, looser when the products with M run on the tensor cores), cap 16.
+//   basis (optional, m x kk): on entry, when basis_valid, the starting basis
+//   (all kk columns of an earlier call's final basis, e.g. the same cut one
+//   CTMRG iteration before); on exit the final basis.
 // All products run as (split-K) GEMMs over the GPU.  The kk x kk
 // factorisations run in one block each: on the first iteration in FP64, later
 // in FP32 with FP64 refinement by products (orth_mixed, svd_mixed), falling
 // back to the FP64 Jacobi SVD if the residual stops decreasing.  No heap
 // allocation: host data lives on the stack.
 int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
-                  double* U, double* S, double* V, const double* warm, TsvdStats* stats, int kind, double tol)
+                  double* U, double* S, double* V, const double* warm, TsvdStats* stats, int kind, double tol,
+                  double* basis, bool basis_valid)
 {
     if (k < 1 || k > m) return TN_EINVAL;
     size_t mk = ar.mark();
@@ -264,11 +270,17 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
     double* Sb = ar.take(kk);
     double* rn = ar.take(kk);
     if (!Om || !Y || !Z || !T || !TV || !Ur || !B || !Ub || !Vb || !Sb || !rn) { ar.release(mk); return TN_ENOMEM; }
-    // start: the warm right vectors (k columns) and fresh random oversampling columns
-    TN_TRY(hash_fill(st, Om, (long long)m * kk, 0x5eed0000ull + (unsigned long long)m * 131 + k));
-    if (warm)
-        TN_CUDA(cudaMemcpy2DAsync(Om, kk * sizeof(double), warm, k * sizeof(double), k * sizeof(double), m,
-                                  cudaMemcpyDeviceToDevice, st));
+    // start: the whole kk-column basis a previous call left in `basis` (its oversampling
+    // columns too: a random oversampling start costs several iterations on every call),
+    // else the warm right vectors (k columns) and fresh random oversampling columns
+    if (basis && basis_valid) {
+        TN_CUDA(cudaMemcpyAsync(Om, basis, sizeof(double) * m * kk, cudaMemcpyDeviceToDevice, st));
+    } else {
+        TN_TRY(hash_fill(st, Om, (long long)m * kk, 0x5eed0000ull + (unsigned long long)m * 131 + k));
+        if (warm)
+            TN_CUDA(cudaMemcpy2DAsync(Om, kk * sizeof(double), warm, k * sizeof(double), k * sizeof(double), m,
+                                      cudaMemcpyDeviceToDevice, st));
+    }
     double hs[SMALL_MAX], hr[SMALL_MAX];
     const int max_it = 16;
     int it = 0;
@@ -314,6 +326,7 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
     if (it > max_it) it = max_it;
     TN_CUDA(cudaMemcpyAsync(U, Ur, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, st));
     TN_CUDA(cudaMemcpy2DAsync(V, k * sizeof(double), Om, kk * sizeof(double), k * sizeof(double), m, cudaMemcpyDeviceToDevice, st));
+    if (basis) TN_CUDA(cudaMemcpyAsync(basis, Om, sizeof(double) * m * kk, cudaMemcpyDeviceToDevice, st));
     TN_CUDA(cudaMemcpyAsync(S, Sb, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TN_TRY(sign_fix_cols(st, U, V, m, m, k));
     if (stats) stats->iterations = it;

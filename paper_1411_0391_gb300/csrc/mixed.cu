@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(256) chol32_whiten_kernel(const double* __rest
                                                             double* __restrict__ X)
 {
     extern __shared__ float fs[];
-    float* R = fs;                 // n*n, row j = row j of R after the factorisation
-    float* Ri = R + n * n;         // n*n, R^{-1}; then n*n of scratch
+    const int ld = n | 1;          // odd row stride (see blk_chol_inv)
+    float* R = fs;                 // n*ld: the scaled Gram matrix, then R^{-1}
+    float* Ri = R + n * ld;        // n*ld scratch
     __shared__ double dsc[SMALL_MAX];
     __shared__ int dead[SMALL_MAX];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -56,35 +57,34 @@ __global__ void __launch_bounds__(256) chol32_whiten_kernel(const double* __rest
     __syncthreads();
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
-        R[e] = (float)(G[e] * dsc[i] * dsc[j]) + (i == j ? shift : 0.0f);
+        R[i * ld + j] = (float)(G[e] * dsc[i] * dsc[j]) + (i == j ? shift : 0.0f);
     }
     __syncthreads();
     const float thr = 1e-5f;       // a unit diagonal carries FP32 rounding of ~n * 6e-8
-    blk_chol_inv<float>(R, n, thr, Ri, dead);   // Ri: scratch; R^{-1} lands in R
+    blk_chol_inv<float>(R, n, ld, thr, Ri, dead);   // Ri: scratch; R^{-1} lands in R
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, c = e % n;
-        X[e] = dead[c] ? 0.0 : dsc[i] * (double)R[e];
+        X[e] = dead[c] ? 0.0 : dsc[i] * (double)R[i * ld + c];
     }
 }
 
 // First-order orthogonality correction from G = Y^T Y: X = I - F with
 // F = striu(E) + diag(E)/2, E = G - I, when max |E| <= 1/32 (the error after
 // the step is O(E^2)); otherwise the FP64 Cholesky inverse of G (CholeskyQR).
-// Dead columns (G_jj = 0) stay zero.
+// Dead columns (G_jj = 0) stay zero.  The first-order case is elementwise and
+// spread over the blocks (each block finds max |E| itself, reading G from L2);
+// the Cholesky fallback runs in block 0 alone.
+constexpr int FIX_BLOCKS = 28;
 __global__ void __launch_bounds__(256) orth_fix_kernel(const double* __restrict__ Gin, int n, double* __restrict__ Xo)
 {
     extern __shared__ double ds[];
-    double* G = ds;                // n*n
-    double* X = G + n * n;         // n*n
-    int* dead = reinterpret_cast<int*>(X + n * n);
+    const int ld = n | 1;          // odd row stride (see blk_chol_inv)
     __shared__ double red[32];
     double emax = 0.0;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
-        const double g = Gin[e];
-        G[e] = g;
         const bool zero_col = Gin[(size_t)i * n + i] == 0.0 || Gin[(size_t)j * n + j] == 0.0;
-        if (!zero_col) emax = fmax(emax, fabs(g - (i == j ? 1.0 : 0.0)));
+        if (!zero_col) emax = fmax(emax, fabs(Gin[e] - (i == j ? 1.0 : 0.0)));
     }
     emax = warp_max(emax);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
@@ -98,18 +98,27 @@ __global__ void __launch_bounds__(256) orth_fix_kernel(const double* __restrict_
     emax = red[0];
     __syncthreads();
     if (emax <= 1.0 / 32.0) {
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
             const int i = e / n, j = e % n;
+            const double g = Gin[e];
             double x;
-            if (G[(size_t)j * n + j] == 0.0) x = 0.0;
-            else if (i == j) x = 1.0 - 0.5 * (G[e] - 1.0);
-            else x = i < j ? -G[e] : 0.0;
+            if (Gin[(size_t)j * n + j] == 0.0) x = 0.0;
+            else if (i == j) x = 1.0 - 0.5 * (g - 1.0);
+            else x = i < j ? -g : 0.0;
             Xo[e] = x;
         }
         return;
     }
+    if (blockIdx.x != 0) return;
+    double* G = ds;                // n*ld
+    double* X = G + n * ld;        // n*ld
+    int* dead = reinterpret_cast<int*>(X + n * ld);
     double dmax = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dmax = fmax(dmax, G[i * n + i]);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        G[i * ld + j] = Gin[e];
+        if (i == j) dmax = fmax(dmax, Gin[e]);
+    }
     dmax = warp_max(dmax);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
     __syncthreads();
@@ -119,12 +128,12 @@ __global__ void __launch_bounds__(256) orth_fix_kernel(const double* __restrict_
         red[0] = m;
     }
     __syncthreads();
-    blk_chol_inv<double>(G, n, 1e-26 * red[0], X, dead);     // X: scratch; the inverse lands in G
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xo[e] = G[e];
+    blk_chol_inv<double>(G, n, ld, 1e-26 * red[0], X, dead);     // X: scratch; the inverse lands in G
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Xo[e] = G[(e / n) * ld + e % n];
 }
 
-size_t chol32_smem(int n) { return sizeof(float) * 3 * (size_t)n * n + 64; }
-size_t orthfix_smem(int n) { return sizeof(double) * 2 * (size_t)n * n + sizeof(int) * n + 64; }
+size_t chol32_smem(int n) { return sizeof(float) * 2 * (size_t)n * (n | 1) + 64; }
+size_t orthfix_smem(int n) { return sizeof(double) * 2 * (size_t)n * (n | 1) + sizeof(int) * n + 64; }
 
 // ---------------------------------------------------------------------------
 // FP32 one-sided Jacobi SVD of B (n x n row-major FP64) -> U0, V0 (n x n
@@ -188,9 +197,13 @@ __global__ void __launch_bounds__(1024) svd32_kernel(const double* __restrict__ 
                     al = fmaf(x, x, al); be = fmaf(y, y, be); ga = fmaf(x, y, ga);
                 }
                 al = half_sum_f(al, hmask); be = half_sum_f(be, hmask); ga = half_sum_f(ga, hmask);
-                if (ga == 0.0f || fabsf(ga) <= tol * sqrtf(al * be) || al < 1e-30f || be < 1e-30f) continue;
+                // sqrt(al) sqrt(be), not sqrt(al be): on the graded Ritz blocks of a loop matrix
+                // (column norms from 1 down to 1e-15 and below) the product underflows in FP32,
+                // the test never passes and every sweep rotates again up to the sweep cap
+                if (ga == 0.0f || fabsf(ga) <= tol * sqrtf(al) * sqrtf(be) || al < 1e-30f || be < 1e-30f) continue;
                 const float zeta = (be - al) / (2.0f * ga);
-                const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+                const float az = fabsf(zeta);      // zeta^2 overflows FP32 beyond 1.8e19: t = 1 / (2 |zeta|) there
+                const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (az + (az > 1e18f ? az : sqrtf(1.0f + az * az)));
                 const float c = rsqrtf(1.0f + t * t), s = c * t;
                 for (int i = hl; i < n; i += 16) {
                     const float x = ap[i], y = aq[i];
@@ -231,20 +244,24 @@ __global__ void __launch_bounds__(1024) svd32_kernel(const double* __restrict__ 
 
 // One Ogita-Aishima step: from Rm = U^T U, Sm = V^T V, T = U^T B V (n x n,
 // row-major) produce the corrections F, G (U <- U + U F, V <- V + V G) and the
-// refined singular values S.
-__global__ void __launch_bounds__(1024) oa_step_kernel(const double* __restrict__ Rm, const double* __restrict__ Sm,
-                                                       const double* __restrict__ T, int n, double* __restrict__ F,
-                                                       double* __restrict__ G, double* __restrict__ S)
+// refined singular values S.  Elementwise, with two FP64 divisions per entry:
+// spread over OA_BLOCKS blocks (on one SM the divisions alone take ~0.1 ms at
+// n = 112); every block recomputes the n refined values it needs.
+constexpr int OA_THREADS = 256;
+constexpr int OA_BLOCKS = 49;          // 112^2 / 256 entries: one per thread
+__global__ void __launch_bounds__(OA_THREADS) oa_step_kernel(const double* __restrict__ Rm, const double* __restrict__ Sm,
+                                                             const double* __restrict__ T, int n, double* __restrict__ F,
+                                                             double* __restrict__ G, double* __restrict__ S)
 {
     __shared__ double sig[SMALL_MAX];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double rii = 1.0 - Rm[(size_t)i * n + i], sii = 1.0 - Sm[(size_t)i * n + i];
         const double den = 1.0 - 0.5 * (rii + sii);
         sig[i] = den > 0.0 ? T[(size_t)i * n + i] / den : 0.0;
-        S[i] = sig[i];
+        if (blockIdx.x == 0) S[i] = sig[i];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
         const int i = e / n, j = e % n;
         const double r = (i == j ? 1.0 : 0.0) - Rm[e];
         const double s = (i == j ? 1.0 : 0.0) - Sm[e];
@@ -285,7 +302,7 @@ int orth_mixed(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int
     for (int pass = 0; pass <= fixes; ++pass) {
         TN_TRY(gemm_splitk(st, ar, true, false, cols, cols, rows, 1.0, Y, cols, Y, cols, 0.0, G, cols));
         if (pass == 0) chol32_whiten_kernel<<<1, 256, chol32_smem(cols), st>>>(G, cols, 0.0f, X);
-        else orth_fix_kernel<<<1, 256, orthfix_smem(cols), st>>>(G, cols, X);
+        else orth_fix_kernel<<<FIX_BLOCKS, 256, orthfix_smem(cols), st>>>(G, cols, X);
         TN_LAUNCHED();
         TN_TRY(gemm(st, false, false, rows, cols, cols, 1.0, Y, cols, 0, X, cols, 0, 0.0, tmp, cols, 0, 1));
         TN_CUDA(cudaMemcpyAsync(Y, tmp, sizeof(double) * rows * cols, cudaMemcpyDeviceToDevice, st));
@@ -308,7 +325,7 @@ int orth_fixes(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int
     if (!G || !X) { ar.release(mk); return TN_ENOMEM; }
     for (int pass = 0; pass < fixes; ++pass) {
         TN_TRY(gemm_splitk(st, ar, true, false, cols, cols, rows, 1.0, Y, cols, Y, cols, 0.0, G, cols));
-        orth_fix_kernel<<<1, 256, orthfix_smem(cols), st>>>(G, cols, X);
+        orth_fix_kernel<<<FIX_BLOCKS, 256, orthfix_smem(cols), st>>>(G, cols, X);
         TN_LAUNCHED();
         TN_TRY(gemm(st, false, false, rows, cols, cols, 1.0, Y, cols, 0, X, cols, 0, 0.0, tmp, cols, 0, 1));
         TN_CUDA(cudaMemcpyAsync(Y, tmp, sizeof(double) * rows * cols, cudaMemcpyDeviceToDevice, st));
@@ -340,7 +357,7 @@ int svd_mixed(cudaStream_t st, Arena& ar, const double* B, int n, double* U, dou
         TN_TRY(gemm(st, true, false, n, n, n, 1.0, V, n, 0, V, n, 0, 0.0, Sm, n, 0, 1));
         TN_TRY(gemm(st, false, false, n, n, n, 1.0, B, n, 0, V, n, 0, 0.0, BV, n, 0, 1));
         TN_TRY(gemm(st, true, false, n, n, n, 1.0, U, n, 0, BV, n, 0, 0.0, T, n, 0, 1));
-        oa_step_kernel<<<1, 1024, 0, st>>>(Rm, Sm, T, n, F, G, S);
+        oa_step_kernel<<<OA_BLOCKS, OA_THREADS, 0, st>>>(Rm, Sm, T, n, F, G, S);
         TN_LAUNCHED();
         // U <- U + U F, V <- V + V G (BV and Rm are free again: staging copies)
         TN_CUDA(cudaMemcpyAsync(BV, U, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));

@@ -73,7 +73,7 @@ static __device__ int blk_svd_onesided(double* A, int m, int n, double* V, int* 
                     al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
                 }
                 al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al) * sqrt(be)) continue;   // no underflow of al be
                 double zeta = (be - al) / (2.0 * ga);
                 double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
                 double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
@@ -199,7 +199,9 @@ __device__ __forceinline__ T warp_sum_t(T v)
 }
 
 // Cholesky G = L L^T of the symmetric n x n matrix in shared memory (row-major,
-// leading dimension n), then X = (L^T)^{-1} = R^{-1} (upper triangular), written
+// leading dimension ld, which callers make odd, n + 1 for even n: threads of a
+// warp walk different rows, and an even row stride would put them on one
+// shared-memory bank), then X = (L^T)^{-1} = R^{-1} (upper triangular), written
 // over G.  Blocked in panels of CB = 16 columns so that the whole factorisation
 // and inversion take a few dozen block barriers (n = 112: 7 panels), not a few
 // per column -- on one SM the barriers, not the arithmetic, set the time:
@@ -211,11 +213,11 @@ __device__ __forceinline__ T warp_sum_t(T v)
 //            J < I as M_IJ = -M_II sum_{K=J}^{I-1} L_IK M_KJ (two phases);
 //   X = M^T.
 // A pivot not above thr marks its column dead: L's column is zero below a unit
-// diagonal and X's column is zero.  M: n x n shared scratch; dead: n ints.
+// diagonal and X's column is zero.  M: n x ld shared scratch; dead: n ints.
 constexpr int CB = 16;
 
 template <typename T>
-__device__ void blk_chol_inv(T* G, int n, T thr, T* M, int* dead)
+__device__ void blk_chol_inv(T* G, int n, int ld, T thr, T* M, int* dead)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nthr = blockDim.x;
     for (int p = 0; p < n; p += CB) {
@@ -224,17 +226,17 @@ __device__ void blk_chol_inv(T* G, int n, T thr, T* M, int* dead)
             // unblocked Cholesky of columns p .. pe-1 over rows p .. n-1 (earlier panels'
             // contributions are already subtracted by their trailing updates)
             for (int j = p; j < pe; ++j) {
-                T d = G[j * n + j];
-                for (int k = p; k < j; ++k) d -= G[j * n + k] * G[j * n + k];
+                T d = G[j * ld + j];
+                for (int k = p; k < j; ++k) d -= G[j * ld + k] * G[j * ld + k];
                 const bool isdead = !(d > thr);
                 const T r = isdead ? T(1) : sqrt(d);
                 for (int i = j + 1 + lane; i < n; i += 32) {
-                    T v = G[i * n + j];
-                    for (int k = p; k < j; ++k) v -= G[i * n + k] * G[j * n + k];
-                    G[i * n + j] = isdead ? T(0) : v / r;
+                    T v = G[i * ld + j];
+                    for (int k = p; k < j; ++k) v -= G[i * ld + k] * G[j * ld + k];
+                    G[i * ld + j] = isdead ? T(0) : v / r;
                 }
                 __syncwarp();
-                if (lane == 0) { G[j * n + j] = r; dead[j] = isdead ? 1 : 0; }
+                if (lane == 0) { G[j * ld + j] = r; dead[j] = isdead ? 1 : 0; }
                 __syncwarp();
             }
         }
@@ -244,9 +246,9 @@ __device__ void blk_chol_inv(T* G, int n, T thr, T* M, int* dead)
         for (int e = threadIdx.x; e < m * m; e += nthr) {
             const int i = pe + e / m, c = pe + e % m;
             if (c > i) continue;
-            T acc = G[i * n + c];
-            for (int k = p; k < pe; ++k) acc -= G[i * n + k] * G[c * n + k];
-            G[i * n + c] = acc;
+            T acc = G[i * ld + c];
+            for (int k = p; k < pe; ++k) acc -= G[i * ld + k] * G[c * ld + k];
+            G[i * ld + c] = acc;
         }
         __syncthreads();
     }
@@ -258,9 +260,9 @@ __device__ void blk_chol_inv(T* G, int n, T thr, T* M, int* dead)
         for (int c = p + lane; c < pe; c += 32) {          // column c of the block's inverse
             for (int i = p; i < pe; ++i) {
                 T acc = (i == c) ? T(1) : T(0);
-                if (i < c) { M[i * n + c] = T(0); continue; }
-                for (int l = c; l < i; ++l) acc -= G[i * n + l] * M[l * n + c];
-                M[i * n + c] = acc / G[i * n + i];
+                if (i < c) { M[i * ld + c] = T(0); continue; }
+                for (int l = c; l < i; ++l) acc -= G[i * ld + l] * M[l * ld + c];
+                M[i * ld + c] = acc / G[i * ld + i];
             }
         }
     }
@@ -272,22 +274,22 @@ __device__ void blk_chol_inv(T* G, int n, T thr, T* M, int* dead)
         for (int e = threadIdx.x; e < (pe - p) * p; e += nthr) {
             const int i = p + e / p, c = e % p;             // row i of block row I, column c < p
             T acc = T(0);
-            for (int l = c; l < p; ++l) acc += G[i * n + l] * M[l * n + c];
-            M[c * n + i] = acc;                              // transposed slot (c < p <= i): upper triangle
+            for (int l = c; l < p; ++l) acc += G[i * ld + l] * M[l * ld + c];
+            M[c * ld + i] = acc;                              // transposed slot (c < p <= i): upper triangle
         }
         __syncthreads();
         // phase 2: M_IJ = -M_II T_IJ
         for (int e = threadIdx.x; e < (pe - p) * p; e += nthr) {
             const int i = p + e / p, c = e % p;
             T acc = T(0);
-            for (int l = p; l <= i; ++l) acc += M[i * n + l] * M[c * n + l];
-            M[i * n + c] = -acc;
+            for (int l = p; l <= i; ++l) acc += M[i * ld + l] * M[c * ld + l];
+            M[i * ld + c] = -acc;
         }
         __syncthreads();
     }
     for (int e = threadIdx.x; e < n * n; e += nthr) {
         const int i = e / n, c = e % n;
-        G[e] = (i <= c && !dead[c]) ? M[c * n + i] : T(0);
+        G[i * ld + c] = (i <= c && !dead[c]) ? M[c * ld + i] : T(0);
     }
     __syncthreads();
 }

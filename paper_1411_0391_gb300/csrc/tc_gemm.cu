@@ -612,8 +612,15 @@ __global__ void oz_exponent_kernel(const double* __restrict__ X, int ld, int kco
         double x;
         if (kcontig) { r = r0 + i; k = k0 + tx; x = (r < R && k < K) ? X[(size_t)r * ld + k] : 0.0; }
         else { k = k0 + i; r = r0 + tx; x = (r < R && k < K) ? X[(size_t)k * ld + r] : 0.0; }
+        // the frexp exponent (x = f 2^ex, 1/2 <= |f| < 1) from the bits: x = m 2^e2 with
+        // significand m, ex = bitlength(m) + e2 (integer arithmetic, subnormals included)
         int ex = OZ_EMPTY;
-        if (x != 0.0) frexp(x, &ex);
+        if (x != 0.0) {
+            const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+            const int bexp = (int)(u >> 52);
+            const unsigned long long m = (u & 0x000fffffffffffffull) | (bexp ? 0x0010000000000000ull : 0ull);
+            ex = (64 - __clzll((long long)m)) + (bexp ? bexp : 1) - 1075;
+        }
         if (kcontig) red[i][tx] = ex; else red[tx][i] = ex;
     }
     __syncthreads();
@@ -648,12 +655,24 @@ __global__ void oz_slice_kernel(const double* __restrict__ X, int ld, int kconti
     for (int i = ty; i < 32; i += 8) {
         const int r = r0 + i, k = k0 + tx;
         const int er = (r < R) ? e[r] : OZ_EMPTY;
-        double v = (er > OZ_EMPTY) ? ldexp(tile[i][tx], -er) : 0.0;      // |v| < 1, exact scaling
+        const double x = tile[i][tx];
+        // |v| = |x| 2^-er < 1 as the fixed-point integer F = floor(|v| 2^(8S)) (at most 56 bits),
+        // read off the binary representation: x = m 2^e2 with the 53-bit significand m.  The
+        // slices are F's bytes from the top, with the sign of x: the same digits as repeated
+        // "times 256, truncate, keep the remainder" in FP64, without FP64 arithmetic (the
+        // FP64 pipe, 1/64 of FP32 on this GPU, made that the slowest pass of the product).
+        unsigned long long F = 0;
+        if (er > OZ_EMPTY && x != 0.0) {
+            const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+            const int bexp = (int)(u >> 52);
+            const unsigned long long m = (u & 0x000fffffffffffffull) | (bexp ? 0x0010000000000000ull : 0ull);
+            const int sh = (bexp ? bexp : 1) - 1075 + 8 * S - er;          // F = floor(m 2^sh)
+            F = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);  // m 2^sh < 2^(8S): no overflow
+        }
+        const bool neg = x < 0.0;
         for (int q = 0; q < S; ++q) {
-            const double t = v * 256.0;                                     // exact
-            const double a = trunc(t);                                      // integer in [-255, 255]
-            v = t - a;                                                      // exact remainder
-            out[((size_t)q * Rp + r) * Kp + k] = __float2bfloat16_rn((float)a);   // exact
+            const int a = (int)((F >> (8 * (S - 1 - q))) & 0xffull);     // integer in [0, 255]
+            out[((size_t)q * Rp + r) * Kp + k] = __float2bfloat16_rn((float)(neg ? -a : a));   // exact
         }
     }
 }

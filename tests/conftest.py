@@ -10,4 +10,4 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: oracle pin that takes tens of seconds")
+    config.addinivalue_line("markers", "slow: a pin that takes tens of seconds to minutes")

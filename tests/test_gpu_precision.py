@@ -16,8 +16,10 @@ FP64.  The bar of the precision form is 1e-6 relative on the energy.
   by the bench.
 The converged corner spectra move with the product error times the conditioning
 of the truncated fixed point (S^{-1/2} of the loop's kept directions):
-3.6e-5 (TF32 x3) and 2.5e-3 (BF16 x3) measured at D = 2, chi = 12; for the
-slices, whose products are ~300x more accurate than TF32 x3's, the bound is 1e-6.
+3.6e-5 (TF32 x3, products ~1e-7) and 2.5e-3 (BF16 x3) measured at D = 2,
+chi = 12, an amplification of ~400 on the value at the truncation edge; for
+the 4-slice products (~4e-9 on Gaussian operands) that model gives ~1.6e-6 on
+that value (1.9e-6 measured on GB300), so the bound is 5e-6.
 """
 import numpy as np
 import pytest
@@ -34,7 +36,7 @@ torch = pytest.importorskip("torch")
 CELL = OC.checkerboard()
 E_TOL = {L.TN_TF32X3: 1e-6, L.TN_BF16X3: 1e-4, L.TN_BF16S4: 1e-6}
 # normalised corner spectra converged in the split form (FP64 start, then split products)
-SPEC_TOL = {L.TN_TF32X3: 1e-4, L.TN_BF16X3: 5e-3, L.TN_BF16S4: 1e-6}
+SPEC_TOL = {L.TN_TF32X3: 1e-4, L.TN_BF16X3: 5e-3, L.TN_BF16S4: 5e-6}
 CTM_TOL = {L.TN_TF32X3: 1e-7, L.TN_BF16X3: 1e-5, L.TN_BF16S4: 1e-11}
 
 
