@@ -67,10 +67,7 @@ static bool plan(Ctx& c)
     c.envbuf = take(c.env_size());
     for (int r = 0; r < 4; ++r)
         for (int x = 0; x < 2; ++x)
-            for (int y = 0; y < 2; ++y) {
-                c.warmV[r][x][y] = take(N * chi);
-                c.warmB[r][x][y] = take(N * (size_t)tsvd_columns((int)N, chi));
-            }
+            for (int y = 0; y < 2; ++y) c.warmV[r][x][y] = take(N * chi);
     for (int y = 0; y < 4; ++y) { c.Pup[y] = take(N * chi); c.Plo[y] = take(N * chi); }
     c.dscratch = take(64);
     c.scratch_base = ar.mark();

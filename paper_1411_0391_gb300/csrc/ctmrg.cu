@@ -166,11 +166,11 @@ static int cut_projectors(Ctx& c, Frame& f, int x, int y, double* Pup, double* P
     TN_TRY(gemm_any(st, ar, kd, false, false, N, N, N, 1.0, Rd, N, Ru, N, 0.0, rho, N));
     const int xx = ((x % f.Lx) + f.Lx) % f.Lx, yy = ((y % f.Ly) + f.Ly) % f.Ly;
     double* Vw = c.warmV[f.rot][xx][yy];
-    // V goes to this cut's slot (P_lo below); the SVD starts from, and leaves, the cut's whole basis
+    // V goes straight into the warm-start slot of this cut
     // the projector SVD runs in FP64 in every mode; its products with rho run on the SIMT
     // pipe or, in the slice forms, as FP64-accurate 7-slice tensor-core products
-    int s = truncated_svd(st, ar, rho, N, chi, U, S, Vw, nullptr, &stats, c.svd_kind(), c.svd_tol(),
-                          c.warmB[f.rot][xx][yy], c.warm_ok[f.rot][xx][yy]);
+    int s = truncated_svd(st, ar, rho, N, chi, U, S, Vw, c.warm_ok[f.rot][xx][yy] ? Vw : nullptr, &stats,
+                          c.svd_kind(), c.svd_tol());
     if (s != TN_OK && s != TN_ENOCONV) return s;
     c.warm_ok[f.rot][xx][yy] = true;
     // P_up = R_d^T U S^{-1/2}, P_lo = R_u V S^{-1/2}

@@ -65,8 +65,7 @@ struct Ctx {
     double* boundary = nullptr;
     double* envbuf = nullptr;
     Env env0[MAXS];            // environment storage in the unrotated frame
-    double* warmV[4][4][4];    // projector right vectors (rotation, x, y)
-    double* warmB[4][4][4];    // the projector SVD's whole final basis (N x kk) per cut, for warm starts
+    double* warmV[4][4][4];    // projector right vectors (rotation, x, y) for warm starts
     bool warm_ok[4][4][4];
     double cut_override = -1.0;   // projector cutoff set by tn_set_projector_cutoff (< 0: default)
     // Precision schedule of the split forms: after an environment reset the

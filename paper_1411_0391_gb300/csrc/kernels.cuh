@@ -42,7 +42,7 @@ int svd_mixed(cudaStream_t st, Arena& ar, const double* B, int n, double* U, dou
 // stopping threshold relative to the largest singular value.
 int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
                   double* U, double* S, double* V, const double* warm, TsvdStats* stats,
-                  int kind = -1, double tol = 1e-13, double* basis = nullptr, bool basis_valid = false);
+                  int kind = -1, double tol = 1e-13);
 
 // tc_gemm.cu: split-precision products on the tensor cores (kind 0 = TF32 x3,
 // 1 = BF16 x3); tc_status reads and clears the device-side wait flag.

@@ -230,17 +230,13 @@ int orth2(cudaStream_t st, Arena& ar, double* Y, double* tmp, int rows, int cols
 //   pair has || M v_i - s_i u_i || = || T vb_i - s_i u_i || <= tol s_1 (an
 //   absolute test: directions at the noise floor pass it too; tol = 1e-13 in
 //   FP64, looser when the products with M run on the tensor cores), cap 16.
-//   basis (optional, m x kk): on entry, when basis_valid, the starting basis
-//   (all kk columns of an earlier call's final basis, e.g. the same cut one
-//   CTMRG iteration before); on exit the final basis.
 // All products run as (split-K) GEMMs over the GPU.  The kk x kk
 // factorisations run in one block each: on the first iteration in FP64, later
 // in FP32 with FP64 refinement by products (orth_mixed, svd_mixed), falling
 // back to the FP64 Jacobi SVD if the residual stops decreasing.  No heap
 // allocation: host data lives on the stack.
 int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
-                  double* U, double* S, double* V, const double* warm, TsvdStats* stats, int kind, double tol,
-                  double* basis, bool basis_valid)
+                  double* U, double* S, double* V, const double* warm, TsvdStats* stats, int kind, double tol)
 {
     if (k < 1 || k > m) return TN_EINVAL;
     size_t mk = ar.mark();
@@ -270,17 +266,11 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
     double* Sb = ar.take(kk);
     double* rn = ar.take(kk);
     if (!Om || !Y || !Z || !T || !TV || !Ur || !B || !Ub || !Vb || !Sb || !rn) { ar.release(mk); return TN_ENOMEM; }
-    // start: the whole kk-column basis a previous call left in `basis` (its oversampling
-    // columns too: a random oversampling start costs several iterations on every call),
-    // else the warm right vectors (k columns) and fresh random oversampling columns
-    if (basis && basis_valid) {
-        TN_CUDA(cudaMemcpyAsync(Om, basis, sizeof(double) * m * kk, cudaMemcpyDeviceToDevice, st));
-    } else {
-        TN_TRY(hash_fill(st, Om, (long long)m * kk, 0x5eed0000ull + (unsigned long long)m * 131 + k));
-        if (warm)
-            TN_CUDA(cudaMemcpy2DAsync(Om, kk * sizeof(double), warm, k * sizeof(double), k * sizeof(double), m,
-                                      cudaMemcpyDeviceToDevice, st));
-    }
+    // start: the warm right vectors (k columns) and fresh random oversampling columns
+    TN_TRY(hash_fill(st, Om, (long long)m * kk, 0x5eed0000ull + (unsigned long long)m * 131 + k));
+    if (warm)
+        TN_CUDA(cudaMemcpy2DAsync(Om, kk * sizeof(double), warm, k * sizeof(double), k * sizeof(double), m,
+                                  cudaMemcpyDeviceToDevice, st));
     double hs[SMALL_MAX], hr[SMALL_MAX];
     const int max_it = 16;
     int it = 0;
@@ -326,7 +316,6 @@ int truncated_svd(cudaStream_t st, Arena& ar, const double* M, int m, int k,
     if (it > max_it) it = max_it;
     TN_CUDA(cudaMemcpyAsync(U, Ur, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, st));
     TN_CUDA(cudaMemcpy2DAsync(V, k * sizeof(double), Om, kk * sizeof(double), k * sizeof(double), m, cudaMemcpyDeviceToDevice, st));
-    if (basis) TN_CUDA(cudaMemcpyAsync(basis, Om, sizeof(double) * m * kk, cudaMemcpyDeviceToDevice, st));
     TN_CUDA(cudaMemcpyAsync(S, Sb, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TN_TRY(sign_fix_cols(st, U, V, m, m, k));
     if (stats) stats->iterations = it;
