@@ -53,6 +53,10 @@ MAIN_FORMS = ("f64s7", "f64", "bf16s4")      # timed with the full schedule; the
 # step in the FP64-accurate forms on GB300, see the bench line's "k_ctm")
 REF_MOVES_PER_STEP = 70
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor rate
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one oz_gemm_kernel<7> launch at
+# 1024^3, from an ncu capture of `bench.py --profile-gemm` on GB300: the 7 BF16 slices of each
+# operand read once (2 x 14.7 MB); the 8 MB result stays in L2 within the launch
+OZ7_TRAFFIC_1024 = 29426176 + 0
 FP64_PROBE_ITERS = 4096
 
 
@@ -548,7 +552,10 @@ def run_gpu(args):
                                                   "%dx%dx%d incl. exponent and slice passes, launched alone at the "
                                                   "step's N^3 shape" % (N, N, N),
                      "achieved": method_flop / t_tc["f64s7"] / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
-                     "frac": method_flop / t_tc["f64s7"] / 1e12 / bf16_peak, "traffic": None,
+                     "frac": method_flop / t_tc["f64s7"] / 1e12 / bf16_peak,
+                     "traffic": OZ7_TRAFFIC_1024 if N == 1024 else None,
+                     "traffic_scope": "oz_gemm_kernel<7> alone (the exponent and slice passes are timed, not "
+                                      "counted); algorithmic: 2 x 7 slices x N^2 x 2 B read + 8 N^2 B written",
                      "flop_basis": "method FLOPs 2N^3 of the FP64 product it delivers; the tensor pipe executes "
                                    "28 slice products (56 N^3)",
                      "pipe_frac": 28 * method_flop / t_tc["f64s7"] / 1e12 / bf16_peak,
