@@ -132,3 +132,31 @@ def test_evolve_options_validated_on_host(libpath):
         assert L.tn_evolve(ctx, 4, ctypes.byref(o), ctypes.byref(rep)) == _lib.TN_EINVAL
     assert L.tn_evolve(None, 4, ctypes.byref(cases[1]), ctypes.byref(rep)) == _lib.TN_EINVAL
     assert b"unstable" in L.tn_strerror(_lib.TN_EUNSTABLE)
+
+
+def test_batch_imps_and_autotune_validated_on_host(libpath):
+    """The batched runner, the 1D chain and the autotuner switch check their arguments on the
+    host: malformed calls return TN_EINVAL without a device call."""
+    from paper_1411_0391_gb300 import _lib
+    L = _lib.lib()
+    o = _lib.tn_evolve_opts(_lib.TN_RECYCLE_OFF, 1, 1e-8, 10, 0.0, 1, 0, 1e-12, 50, 0.0)
+    st = (ctypes.c_int * 2)()
+    reps = (_lib.tn_evolve_report * 2)()
+    assert L.tn_evolve_batch(None, 2, 1, ctypes.byref(o), 0, st, reps) == _lib.TN_EINVAL
+    two_null = (ctypes.c_void_p * 2)(None, None)
+    assert L.tn_evolve_batch(two_null, 2, 1, ctypes.byref(o), 0, st, reps) == _lib.TN_EINVAL
+    assert L.tn_evolve_batch(two_null, 0, 1, ctypes.byref(o), 0, st, reps) == _lib.TN_EINVAL
+    assert L.tn_evolve_batch(two_null, 2, 1, None, 0, st, reps) == _lib.TN_EINVAL
+    # 1D chain: bond 2 chi <= 32; workspace sizes are host arithmetic
+    assert L.tn_imps_workspace_bytes(0) == 0 and L.tn_imps_workspace_bytes(17) == 0
+    assert 0 < L.tn_imps_workspace_bytes(4) < L.tn_imps_workspace_bytes(16)
+    F = ctypes.c_double()
+    out = (ctypes.c_double * 3)()
+    assert L.tn_imps_itebd(None, 4, 2.0, 0.05, 1, None, 0, None) == _lib.TN_EINVAL
+    assert L.tn_imps_itebd(None, 4, float("nan"), 0.05, 1, None, 0, None) == _lib.TN_EINVAL
+    assert L.tn_imps_recycle(None, 4, 2.0, 0.05, 0, ctypes.byref(F), None, 0, None) == _lib.TN_EINVAL
+    assert L.tn_imps_observables(None, 4, 2.0, out, None, 0, None) == _lib.TN_EINVAL
+    assert L.tn_imps_observables(None, 4, 2.0, None, None, 0, None) == _lib.TN_EINVAL
+    # the tile autotuner switch: on/off, returns the number of shapes tuned so far
+    n0 = L.tn_set_autotune(1)
+    assert n0 >= 0 and L.tn_set_autotune(0) == n0
