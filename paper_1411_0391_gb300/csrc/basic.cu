@@ -146,22 +146,23 @@ static int tuned_tile(cudaStream_t st, bool ta, bool tb, int m, int n, int k, do
     const int cand[3] = {16, 32, 64};
     float best = 1e30f;
     int pick = gemm_tile(m, n, batch);
-    cudaEvent_t e0, e1;
-    TN_CUDA(cudaEventCreate(&e0));
-    TN_CUDA(cudaEventCreate(&e1));
+    struct Events {               // destroyed on every return path
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events() { for (cudaEvent_t x : e) if (x) cudaEventDestroy(x); }
+    } ev;
+    TN_CUDA(cudaEventCreate(&ev.e[0]));
+    TN_CUDA(cudaEventCreate(&ev.e[1]));
     for (int c = 0; c < 3; ++c) {
         if ((m + cand[c] - 1) / cand[c] > 65535) continue;
-        TN_CUDA(cudaEventRecord(e0, st));
+        TN_CUDA(cudaEventRecord(ev.e[0], st));
         launch_tile(cand[c], st, ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, 0.0, C, ldc, sC, batch);
         TN_LAUNCHED();
-        TN_CUDA(cudaEventRecord(e1, st));
-        TN_CUDA(cudaEventSynchronize(e1));
+        TN_CUDA(cudaEventRecord(ev.e[1], st));
+        TN_CUDA(cudaEventSynchronize(ev.e[1]));
         float ms = 0.0f;
-        TN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        TN_CUDA(cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]));
         if (ms < best) { best = ms; pick = cand[c]; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = pick;
