@@ -286,7 +286,9 @@ size_t tn_imps_workspace_bytes(int chi);
 int tn_imps_itebd(double* dA, int chi, double h, double tau, int n_steps, void* work, size_t bytes, void* stream);
 /* One recycling window (Sec. V.B): A_0 = weighted canonical form of A; one
  * plain step gives A~ = Q (g A_0) P; the canonical form of A~ gives its maps;
- * gauge fixing finds U with A~_1 ~ U A_0 U^T (fidelity F, optional out); the
+ * gauge fixing (Sec. III.B.2, started from the polar factor of the kappa = 0
+ * block of the leg map Q_c Q) finds U with A~_1 ~ U A_0 U^T (fidelity F,
+ * optional out); the
  * renormalised gate G = U^T Q_c Q g P P_c U is applied n_re times to A_0.
  * A is replaced by A_{n_re}. */
 int tn_imps_recycle(double* dA, int chi, double h, double tau, int n_re, double* fidelity, void* work,
