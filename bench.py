@@ -241,9 +241,10 @@ def energy_error_small(L, precision):
     return abs(g["e_site"] - o["e_site"]) / abs(o["e_site"]), g["e_site"], o["e_site"]
 
 
-def time_form(L, torch, dev, stream, name, state, warmup, flush, steps, recycled=True, fixed=True):
-    """Warm-up, then `steps` timed converged steps (and optionally `steps` recycled windows
-    and `steps` fixed-budget steps) of one precision form."""
+def time_form(L, torch, dev, stream, name, state, warmup, flush, steps, recycled=True, fixed=True, e2e=False):
+    """Warm-up, then `steps` timed converged steps (and optionally `steps` end-to-end steps
+    through the public API, `steps` fixed-budget steps and `steps` recycled windows) of one
+    precision form."""
     D, chi = WL["D"], WL["chi"]
     tol = CTM_TOL[name]
     ctx = L.Context(D, chi, device=dev, precision=PRECISIONS[name])
@@ -281,6 +282,19 @@ def time_form(L, torch, dev, stream, name, state, warmup, flush, steps, recycled
                ctm_tol=tol, steps_total=warmup + steps)
     import numpy as np
     out["state"] = [np.ascontiguousarray(a) for a in ctx.tn_get_state()]    # after the converged steps
+    if e2e:
+        # end to end through the public API with host buffers, continuing the same converged
+        # trajectory: H2D of the state, one converged step (tn_fu_step), D2H of the result
+        host = [np.ascontiguousarray(a) for a in out["state"]]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.tn_set_state(host)
+            ctx.tn_fu_step(tol, CTM_MAX)
+            host = ctx.tn_get_state()
+        torch.cuda.synchronize()
+        out["t_e2e"] = time.perf_counter() - t0
+        out["e2e_bytes"] = sum(a.nbytes for a in host)
     if fixed:
         # the fixed-budget step (FIXED_CTM_ITERS iterations, no convergence test): secondary
         t_fix = 0.0
@@ -462,25 +476,14 @@ def run_gpu(args):
             steps = args.steps if main else max(1, min(args.steps, 3))
             warm = args.warmup if main else min(args.warmup, 1)
             ctxs[name], results[name] = time_form(L, torch, dev, stream, name, state, warm, flush, steps,
-                                                  recycled=name in (HEADLINE, "f64"), fixed=name == HEADLINE)
+                                                  recycled=name in (HEADLINE, "f64"), fixed=name == HEADLINE,
+                                                  e2e=name == HEADLINE)
     head = results[HEADLINE]
     total, t_ctm = max_over_ranks([head["total"], head["t_ctm"]], dist, dev)
     value = whole_job_rate(world, args.steps, total)
 
-    import numpy as np
-    # end to end through the public API with host buffers: H2D of the state, one converged
-    # step (tn_fu_step), D2H of the result
-    ctx = ctxs[HEADLINE]
-    host = [np.ascontiguousarray(a) for a in ctx.tn_get_state()]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.tn_set_state(host)
-        ctx.tn_fu_step(CTM_TOL[HEADLINE], CTM_MAX)
-        host = ctx.tn_get_state()
-    torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
-    state_bytes = sum(a.nbytes for a in host)
+    e2e_t = max_over_ranks([head["t_e2e"]], dist, dev)[0]
+    state_bytes = head["e2e_bytes"]
     for c in ctxs.values():
         c.close()
 
