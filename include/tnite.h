@@ -59,10 +59,12 @@ extern "C" {
 #define TN_BF16X3 2   /* split-precision tensor-core products, BF16 head + tail (tn_gemm_split) */
 #define TN_BF16S4 3   /* exact-accumulation tensor-core products: 4 BF16 integer slices per operand
                          (the Ozaki scheme), 10 slice products, FP32 accumulation that is exact
-                         by construction; error < 2^-30 of the row/column scales (tn_gemm_split) */
+                         by construction; error per term of the K sum below 5 * 2^-32 of the
+                         row/column scales (tn_gemm_split) */
 #define TN_F64S7  4   /* FP64-accurate tensor-core products: 7 BF16 integer slices per operand,
-                         28 slice products, exact accumulation; error below 2^-54 of the
-                         row/column scales, the unit roundoff of FP64 (tn_gemm_split) */
+                         28 slice products, exact accumulation; error per term below
+                         8 * 2^-56 = 2^-53 of the row/column scales, the unit roundoff of
+                         FP64 (tn_gemm_split) */
 
 typedef struct tn_config {
     int D;          /* PEPS bond dimension, 1..8 */
@@ -339,12 +341,13 @@ int tn_gemm_f64(int transA, int transB, int m, int n, int k, double alpha,
  * into head and tail of the tensor-core type, x = hi + lo, and
  * hi.hi + hi.lo + lo.hi is accumulated in FP32 (about 2^-21 relative for
  * TF32, 2^-16 for BF16).  TN_BF16S4: each row of op(A) and column of op(B)
- * is scaled by a power of two and cut into four 8-bit integer slices held
- * exactly in BF16; the ten slice products of the four leading levels are
- * accumulated exactly (integers below 2^24 in FP32, combined in 64-bit
- * integers), so the error is that of the dropped slices, < 2^-30 of
- * max|A_i.| max|B_.j| K.  TN_F64S7: the same with seven slices (28
- * products), error < 2^-54 of max|A_i.| max|B_.j| K.  C is written in FP64.
+ * is scaled by a power of two and cut (by truncation) into four 8-bit
+ * integer slices held exactly in BF16; the ten slice products of the four
+ * leading levels are accumulated exactly (integers below 2^24 in FP32,
+ * combined in 64-bit integers), so the error is that of the dropped levels,
+ * < 20 * 2^-32 (about 2^-27.7) of max|A_i.| max|B_.j| K.  TN_F64S7: the same
+ * with seven slices (28 products), error < 2^-51 of max|A_i.| max|B_.j| K,
+ * the FP64 rounding level of a K-term sum.  C is written in FP64.
  * This is the contraction arithmetic of the precision form (the paper itself
  * works in double throughout).  d_workspace (device, 256-byte aligned, caller
  * owned) holds the split operands: at least tn_gemm_split_workspace_bytes().

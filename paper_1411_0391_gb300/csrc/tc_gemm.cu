@@ -365,33 +365,38 @@ __global__ void split_kernel(const double* __restrict__ X, int ld, int kcontig, 
 // of matrix multiplication and its applications", Numer. Algorithms 59, 2012).
 //
 // Row i of op(A) is scaled by 2^-e_i, e_i the binary exponent of its largest
-// |entry| (so every scaled entry lies in (-1, 1)), and cut into S = 4 slices
-// of 8 bits by rounding to nearest:  A_ik = 2^e_i sum_s a^(s)_ik 2^-8(s+1) + r_ik,
-// a^(0) an integer in [-256, 256], the later a^(s) in [-128, 128] (all exact in
-// BF16, which carries 8 significant bits), |r_ik| <= 2^(e_i - 33); likewise the
-// columns of op(B) with exponents f_j.  The product is
-//     C_ij = 2^(e_i + f_j - 16) sum_L 2^-8L  P_L,   P_L = sum_{s+t=L} a^(s) b^(t)
-// over the levels L = 0..3 (10 slice products).  Every product of two slices
-// is an integer of at most 2^16, and a level's partial sum over one 64-deep
-// K block stays within 64 * (2 * 2^15 + 2 * 2^14) < 2^24 (level 3, the largest):
-// the FP32 tensor-core accumulator holds it exactly, whatever its rounding.  Each
-// block's level sums are read from tensor memory, converted to integers (exact)
-// and combined into one 64-bit integer per element,
-//     Q += P_0 2^24 + P_1 2^16 + P_2 2^8 + P_3,
-// so the only rounding of the whole product is the final conversion of Q to
-// double.  The dropped slices and levels leave, per term of the K sum, less
-// than 4 * 2^-33 of the scale 2^(e_i + f_j) <= 4 max|A_i.| max|B_.j|.
+// |entry| (so every scaled entry lies in (-1, 1)), and cut into S slices of
+// 8 bits by truncation:  A_ik = 2^e_i sum_{s<S} a^(s)_ik 2^-8(s+1) + r_ik, the
+// a^(s) integers in [0, 255] carrying the sign of A_ik (exact in BF16, which
+// holds 8 significant bits), |r_ik| < 2^(e_i - 8S); likewise the columns of
+// op(B) with exponents f_j.  The product keeps the levels L = s + t < S,
+//     C_ij = 2^(e_i + f_j - 16) sum_{L<S} 2^-8L  P_L,   P_L = sum_{s+t=L} a^(s) b^(t)
+// (S (S+1) / 2 slice products).  Every product of two slices is an integer of
+// magnitude below 2^16, and level L (L + 1 products) summed over one K block of
+// KROW elements stays below (L + 1) KROW 255^2 < 2^24 (4 slices, KROW = 64,
+// level 3: 16 646 400; 7 slices, KROW = 32, level 6: 14 565 600): the FP32
+// tensor-core accumulator holds it exactly, whatever its rounding.  Each block's
+// level sums are read from tensor memory, converted to integers (exact) and
+// added into 64-bit integers, levels 0..H-1 into one and the rest into a second,
+//     Q_0 += sum_{L<H} P_L 2^8(H-1-L),   Q_1 += sum_{L>=H} P_L 2^8(S-1-L),
+// so the only roundings are the final conversions of Q_0, Q_1 to double (exact
+// while they stay below 2^53: for K <= 8192 with 4 slices, K <= 2048 for Q_1
+// with 7 slices; beyond, a rounding at the FP64 unit roundoff of the partial
+// sum).  The dropped levels L >= S (all pairs s + t = L, slices beyond S
+// included) leave, per term of the K sum, at most
+//     2^(e_i + f_j) 255^2 2^-16 sum_{L>=S} (L + 1) 2^-8L  <  (S + 1) 2^-8S 2^(e_i + f_j),
+// and 2^(e_i + f_j) <= 4 max|A_i.| max|B_.j|, so
+//     |C - AB|_ij < 4 (S + 1) 2^-8S K max|A_i.| max|B_.j|
+// (4 slices: 20 * 2^-32 ~ 2^-27.7; 7 slices: 32 * 2^-56 = 2^-51, the FP64 unit
+// roundoff level of a K-term sum).  On Gaussian operands the per-term errors
+// partly cancel, ~1e-9 relative (4 slices).
 // ---------------------------------------------------------------------------
-// Two configurations: 4 slices (10 products; ~2^-33 of the scales) for the
-// precision form, and 7 slices (28 products; below the FP64 unit roundoff of
-// the scales, 2^-57) for FP64-accurate products.  A K block of KROW elements is
-// one shared-memory row per operand row (128-byte rows with 128-byte swizzle
+// Two configurations: 4 slices (10 products) for the precision form, and 7
+// slices (28 products) for FP64-accurate products.  A K block of KROW elements
+// is one shared-memory row per operand row (128-byte rows with 128-byte swizzle
 // for 4 slices, 64-byte rows with 64-byte swizzle for 7, so that three stages
-// fit); its level sums stay below 2^24 (4 slices: 64 * (2*2^15 + 2*2^14) for
-// level 3; 7 slices: 32 * (2*2^15 + 5*2^14) for level 6) and are drained after
-// every K block.  Levels 0..H-1 are combined into one 64-bit integer and the
-// rest into a second (H = 4 for 4 slices: one integer; H = 3 for 7 slices),
-// each below 2^53 for K <= 2^10 * 64, so both convert to double exactly.
+// fit) and is drained after every K block.  H = 4 for 4 slices (one integer),
+// H = 3 for 7 slices.
 template <int S> struct OzCfg;
 template <> struct OzCfg<4> {
     static constexpr int BN = 64, KROW = 64, STAGES = 2, H = 4, SWZ = 2;    // 128-byte swizzle

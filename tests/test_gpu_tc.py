@@ -7,14 +7,14 @@ roundoff of the head type (2^-11 TF32, 2^-8 BF16) plus FP32 accumulation,
 (|A| |B|)_ij and in relative Frobenius norm.
 
 The integer-slice form (Ozaki scheme, TN_BF16S4) accumulates exactly; its only
-error is the dropped slices: per term < 4 * 2^-33 of 2^(e_i + f_j) <=
-4 max|A_i.| max|B_.j|, i.e. |C - AB|_ij < 8 * 2^-32 * K * max|A_i.| * max|B_.j|
-(the bound tested below keeps a factor 2.5 above it).  For Gaussian operands the
-per-term errors are independent and unbiased (round-to-nearest slices), so
-relative to |C| ~ sqrt(K) the Frobenius error is about 2^-33 times the ratio of
-the row/column scale to a typical entry (~4 for Gaussian rows): ~1e-9, bounded
-at 1e-8.  On integer operands that the slices hold exactly the product must
-come out exact.
+error is the dropped levels of the truncated 8-bit slices: per term
+< (S + 1) 2^-8S of 2^(e_i + f_j) <= 4 max|A_i.| max|B_.j|, i.e. for S = 4
+|C - AB|_ij < 20 * 2^-32 * K * max|A_i.| * max|B_.j| (the bound tested below).
+Truncation biases each term's error toward zero magnitude, but the signs of the
+terms vary, so relative to |C| ~ sqrt(K) the Frobenius error on Gaussian
+operands is about 2^-32 times the ratio of the row/column scale to a typical
+entry (~4 for Gaussian rows): ~1e-9, bounded at 1e-8.  On integer operands that
+the slices hold exactly the product must come out exact.
 """
 import numpy as np
 import pytest
