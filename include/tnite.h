@@ -248,9 +248,10 @@ int tn_evolve(void* ctx, int n_steps, const tn_evolve_opts* opts, tn_evolve_repo
  * by a pool of min(n_threads, n_ctx) host threads (n_threads <= 0: one per
  * context), so the kernels of different instances run concurrently on the
  * GPU.  statuses[i], reps[i] (optional, n_ctx entries) receive each tn_evolve
- * result.  Returns TN_OK when every instance returned TN_OK or TN_EUNSTABLE,
- * else the first other status.  No other thread may use the contexts while
- * the call runs. */
+ * result.  Every context must live on the device that is current in the
+ * calling thread (the worker threads make that device current).  Returns
+ * TN_OK when every instance returned TN_OK or TN_EUNSTABLE, else the first
+ * other status.  No other thread may use the contexts while the call runs. */
 int tn_evolve_batch(void** ctxs, int n_ctx, int n_steps, const tn_evolve_opts* opts, int n_threads,
                     int* statuses, tn_evolve_report* reps);
 
